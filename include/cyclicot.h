@@ -1,0 +1,226 @@
+/*
+ * cyclicot.h -- C ABI of the GB300 (sm_103a) library for optimal transport
+ * with cyclic symmetry (Takeda, Akagi, Marumo, Niwa, AAAI-24, arXiv 2311.13147).
+ *
+ * Problem (Sec. 3.2, Eq. problem_ROT):  min_T <C,T> + sum_ij phi(T_ij)
+ * subject to T 1 = a, T^T 1 = b, with phi = 0 on x >= 0 (LOT, Eq.
+ * reg_for_original_OT) or phi(x) = eps * x (log x - 1) (EROT, Eq.
+ * reg_for_entropy_ROT; the paper calls eps "lambda").
+ *
+ * Cyclic symmetry (Assumption 1, Sec. 4): the full size is n = N * m, the
+ * marginals are N copies of base blocks, a = (alpha; ...; alpha), and the cost
+ * is block-circulant, block (r, c) = C_{(c - r) mod N}
+ * (Eq. blkstr_cost).  This library takes the first block row
+ * C_base[k] = C[0:m, k*m:(k+1)*m] as a dense float array [N][m][m] (row-major,
+ * k slowest), or the base point coordinates when C_k[i][j] = |x_i - R^k y_j|^2
+ * with R the rotation by 2*pi/N.
+ *
+ * Letters: the paper's d (full size) is n here, its n (cyclic order) is N.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller (for example
+ *   from PyTorch tensors).  float arrays must be 16-byte aligned.  The library
+ *   never allocates memory: scratch space comes from the caller's workspace
+ *   (size from ot_workspace_bytes), and nothing is kept between calls.
+ * - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *   stream.  Every call is asynchronous with respect to the host: results,
+ *   including the ot_result record, are valid after the stream is
+ *   synchronised.
+ * - Marginal inputs a_base, b_base (and a, b for full problems) may have any
+ *   positive mass; they are normalised internally (sums in FP64).  Every entry
+ *   must be > 0 (log-domain iterations); a zero or non-finite entry makes the
+ *   solver report OT_ERR_ARG in ot_result.status.
+ * - Return value: OT_OK when the work was enqueued; otherwise an error code
+ *   for problems detectable on the host (null pointer, bad size, too small a
+ *   workspace, CUDA launch failure).  Errors found on the device (divergence,
+ *   non-finite values, an expired wait) are written to ot_result.status.
+ * - No entry point aborts, traps or exits the process.
+ */
+#ifndef CYCLICOT_H
+#define CYCLICOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define OT_OK                 0
+#define OT_ERR_ARG            1   /* null pointer, m <= 0, N <= 0, eps <= 0, bad mode       */
+#define OT_ERR_NOT_DIVISIBLE  2   /* full size n is not a multiple of the cyclic order N    */
+#define OT_ERR_NOT_CONVERGED  3   /* max_iter reached; outputs hold the last iterate         */
+#define OT_ERR_TIMEOUT        4   /* a bounded device-side wait expired (grid barrier)       */
+#define OT_ERR_NONFINITE      5   /* NaN / Inf met in the iteration                          */
+#define OT_ERR_CUDA           6   /* a CUDA runtime call failed                              */
+#define OT_ERR_WORKSPACE      7   /* workspace pointer NULL or smaller than required         */
+#define OT_ERR_UNSUPPORTED    8   /* size or mode outside what this build supports           */
+
+/* ---- modes ----------------------------------------------------------- */
+#define OT_MIN                0   /* LOT fold, Theorem 1                                     */
+#define OT_SOFTMIN            1   /* EROT fold, Eq. def_Kij in log form                      */
+
+#define OT_PLAN_LOT           0   /* unfold Theorem 1's S* by the smallest argmin            */
+#define OT_PLAN_EROT          1   /* unfold Theorem 2's potentials                           */
+
+#define OT_ADJ_ENVELOPE       0   /* gradient from the converged potentials                 */
+#define OT_ADJ_UNROLLED       1   /* reverse pass through a fixed number of iterations        */
+
+#define OT_FP32_LOG           0   /* FP32 log-domain iterations (default)                    */
+#define OT_BF16_KERNEL_POLISH 1   /* BF16 kernel-domain GEMM iterations, then FP32 polish    */
+
+/* ops for ot_workspace_bytes */
+#define OT_OP_SINKHORN_REDUCED 0
+#define OT_OP_SINKHORN_FULL    1
+#define OT_OP_VALUE_AND_GRAD   2
+#define OT_OP_UNROLLED         3
+
+typedef struct {
+    float eps;                      /* regulariser (> 0)                                   */
+    double tol_l1;                  /* stop when the full-scale row L1 error <= tol_l1     */
+    int max_iter;                   /* iteration cap (>= 1)                                */
+    int check_every;                /* test the stopping rule every k iterations (>= 1)    */
+    int precision;                  /* OT_FP32_LOG (the only value ot_sinkhorn_* take)     */
+    int warm_start;                 /* 1: start from the g passed in (f is recomputed)     */
+    unsigned long long timeout_ns;  /* limit of each device-side wait; 0 = 10 s            */
+    int tile_override;              /* reserved, must be 0                                 */
+    int debug_flags;                /* fault injection for tests; 0 in normal use:
+                                       bit 0 (OT_DEBUG_WITHHOLD_ARRIVAL): block 0 never
+                                       arrives at the first grid barrier, so the other
+                                       blocks' bounded waits expire -> OT_ERR_TIMEOUT   */
+} ot_options;
+
+#define OT_DEBUG_WITHHOLD_ARRIVAL 1
+
+/* Device-written outcome of one solve.  64 bytes, naturally aligned. */
+typedef struct {
+    int iters;              /* completed iterations of the returned state               */
+    int status;             /* OT_OK / OT_ERR_*                                          */
+    double marg_l1;         /* full-scale row L1 error sum_i |(T 1)_i - a_i| of the state  */
+    double marg_l2_col;     /* ||T^T 1 - b||_2 (filled by ot_value_and_grad)             */
+    double value;           /* regularised objective of the full problem (value_and_grad)  */
+    double transport_cost;  /* <C, T> of the full problem (value_and_grad)              */
+    double marg_l1_col;     /* full-scale column L1 error (value_and_grad)               */
+    double reserved[2];
+} ot_result;
+
+/* ---- entry points ------------------------------------------------------ */
+
+/* Library version string, e.g. "cyclicot 0.1 sm_103a". */
+const char* ot_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* ot_status_string(int status);
+
+/* Bytes of workspace that `op` needs for a problem of block size m (reduced
+ * ops) or full size n (full ops), cyclic order N.  Returns 0 for a bad op. */
+size_t ot_workspace_bytes(int op, int m_or_n, int N, const ot_options* opt);
+
+/*
+ * ot_fold_cost -- fold the N cost blocks into the m x m reduced cost.
+ *
+ *  mode = OT_MIN (Theorem 1, Eq. definition_G):
+ *      G[i][j] = min_k C_k[i][j],  kstar[i][j] = smallest k attaining it
+ *      (Eq. optimal_solution_problem_CLOT takes the smallest argmin).  The
+ *      comparison is exact: results are bit-identical to any exact min.
+ *  mode = OT_SOFTMIN (Sec. 5.4, Eq. def_Kij):
+ *      G[i][j] = -eps * log K_ij,  K_ij = sum_k exp(-C_k[i][j] / eps),
+ *      computed as cmin - eps * log sum_k exp(-(C_k[i][j] - cmin)/eps).
+ *      The reduced EROT problem is then a plain m x m EROT on G with
+ *      marginals of mass 1/N; no log N term enters the fold.  kstar unused.
+ *
+ *  Cost source: C_base [N][m][m] if non-NULL; else points x [m][2] (sources)
+ *  and y [m][2] (targets), C_k[i][j] = |x_i - R^k y_j|^2, R = rotation by
+ *  2*pi/N (computed in FP32).
+ *  Outputs: G [m][m] float; kstar [m][m] uint8 (OT_MIN only, N <= 255).
+ */
+int ot_fold_cost(int mode, int m, int N, const float* C_base, const float* x,
+                 const float* y, float eps, float* G, uint8_t* kstar, void* stream);
+
+/*
+ * ot_sinkhorn_reduced -- cyclic Sinkhorn (Algorithm 2) on the folded cost.
+ *
+ * Runs the alternating closed-form dual updates of Eq.
+ * optimal_f_sinkhorn_logdomain in the log domain on the m x m cost G from
+ * ot_fold_cost(OT_SOFTMIN):
+ *     w_i = eps log alpha_i - eps LSE_j((z_j - G_ij)/eps)   (row update)
+ *     z_j = eps log beta_j  - eps LSE_i((w_i - G_ij)/eps)   (column update)
+ * from z = 0 (q = 1), until the full-scale row L1 error
+ * N * sum_i |(S 1)_i - alpha_i| <= opt->tol_l1, where S = sum_k T_k.
+ *
+ *  a_base, b_base [m]: base marginal blocks (any positive mass; alpha =
+ *      a_base / (N * sum a_base)).
+ *  w, z [m] double, out: potentials of the returned state for marginals of
+ *      mass 1/N (the paper's w, z; T_ijk = exp((w_i + z_j - C_ijk)/eps)).
+ *      With opt->warm_start = 1, z is read as the starting point.
+ *  out: device ot_result (iters, status, marg_l1).
+ *  workspace: >= ot_workspace_bytes(OT_OP_SINKHORN_REDUCED, m, N, opt).
+ */
+int ot_sinkhorn_reduced(int m, int N, const float* a_base, const float* b_base, const float* G,
+                        const ot_options* opt, double* w, double* z, ot_result* out,
+                        void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * ot_sinkhorn_full -- plain Sinkhorn on the full n x n problem (the
+ * comparison; Algorithm 3 Stage 2), same iteration and stopping rule.
+ *
+ *  a, b [n]: marginals (normalised internally).
+ *  C [n][n] float if non-NULL; else X [n][2], Y [n][2] and the cost
+ *      C_ij = |X_i - Y_j|^2 is computed on the fly (never stored).
+ *  f, g [n] double, out (g read first when opt->warm_start = 1, e.g. the
+ *      N-fold concatenated Stage-1 potentials of Algorithm 3).
+ */
+int ot_sinkhorn_full(int n, const float* a, const float* b, const float* C,
+                     const float* X, const float* Y, const ot_options* opt,
+                     double* f, double* g, ot_result* out,
+                     void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * ot_unfold_plan -- reconstruct the block-circulant plan.
+ *
+ *  mode = OT_PLAN_LOT (Theorem 1): T_k[i][j] = S[i][j] if k == kstar[i][j]
+ *      else 0.  S_or_w = S [m][m] float (an optimal reduced plan), kstar from
+ *      ot_fold_cost(OT_MIN); z, C_base, x, y unused.
+ *  mode = OT_PLAN_EROT (Algorithm 2's reconstruction, Theorem 2):
+ *      T_k[i][j] = exp((w_i + z_j - C_k[i][j]) / eps); S_or_w = w (double
+ *      [m], cast), z [m] double; cost from C_base or from x, y as in
+ *      ot_fold_cost.
+ *  dense = 0: T is the first block row [N][m][m] (T_0..T_{N-1});
+ *  dense = 1: T is the n x n matrix, T[r*m+i][c*m+j] = T_{(c-r) mod N}[i][j]
+ *      (Lemma 1, Eq. blkstr_optimal_solution).  Index map is exact.
+ */
+int ot_unfold_plan(int mode, int m, int N, const void* S_or_w, const double* z,
+                   const float* C_base, const float* x, const float* y,
+                   const uint8_t* kstar, float eps, int dense, float* T, void* stream);
+
+/*
+ * ot_value_and_grad -- objective, marginal norms and gradients of the EROT
+ * value through the reduced problem.
+ *
+ *  value (out->value): N * [ sum_ijk C_ijk T_ijk + eps T_ijk (log T_ijk - 1) ]
+ *      (Eq. problem_CROT times N, Sec. 5.1), out->transport_cost
+ *      N * sum_ijk C_ijk T_ijk, full-scale row / column L1 and column L2
+ *      marginal errors; all reductions in FP64.
+ *  adjoint = OT_ADJ_ENVELOPE: gradients from Theorem 2's dual at (w, z):
+ *      d_a[m] = dV/da_base = (w - <w,a_base>/s)/s, s = sum a_base (likewise
+ *      d_b with z); d_C [N][m][m] = N * T_k (if C_base given), or
+ *      d_x, d_y [m][2] = 2N sum T_ijk (x_i - R^k y_j), 2N sum T_ijk
+ *      (y_j - R^-k x_i) (if points given).  Any gradient pointer may be NULL.
+ *  adjoint = OT_ADJ_UNROLLED: gradients of V_T = N(<w_T,alpha> + <z_T,beta>)
+ *      - eps after `unroll_iters` iterations from z = 0, by a reverse pass
+ *      that re-reads the folded cost G (which must be passed) and the
+ *      checkpointed potentials; w, z are ignored (the forward pass is rerun).
+ */
+int ot_value_and_grad(int m, int N, const float* a_base, const float* b_base,
+                      const float* C_base, const float* x, const float* y,
+                      const float* G, const double* w, const double* z, float eps,
+                      int adjoint, int unroll_iters, ot_result* out,
+                      float* d_a, float* d_b, float* d_C, float* d_x, float* d_y,
+                      void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CYCLICOT_H */

@@ -1,0 +1,179 @@
+// ot_fold_cost: fold the N cost blocks into the m x m reduced cost.
+//
+// OT_MIN    -- Theorem 1 (Eq. definition_G): G = min_k C_k, kstar = smallest argmin.
+// OT_SOFTMIN-- Eq. def_Kij in log form: G = cmin - eps*log sum_k exp(-(C_k - cmin)/eps).
+//
+// HBM-bound streaming kernel: each thread owns 4 consecutive entries (one
+// 16-byte load per block k), grid-stride over the m*m entries, grid sized to
+// a multiple of the SM count.  With points instead of stored blocks the cost
+// C_k[i][j] = |x_i - R^k y_j|^2 is formed in registers (no HBM traffic for C).
+#include "common.cuh"
+
+namespace cyc {
+
+// min with numpy semantics: a NaN propagates and its first index is kept.
+__device__ __forceinline__ void min_step(float c, int k, float& best, int& kb) {
+    if (best != best) return;
+    if (c != c || c < best) { best = c; kb = k; }
+}
+
+// Online soft-min: keeps s = sum_k exp2((mn - C_k) * kappa) for the running minimum mn.
+__device__ __forceinline__ void softmin_step(float c, float kappa, float& mn, float& s) {
+    if (c < mn) {
+        s = fmaf(s, ex2((c - mn) * kappa), 1.0f);
+        mn = c;
+    } else {
+        s += ex2((mn - c) * kappa);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(OT_BLOCK) fold_blocks_vec4(int N, long long mm4, const float4* __restrict__ C,
+                                                             float kappa, float4* __restrict__ G,
+                                                             uchar4* __restrict__ ks) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mm4; e += stride) {
+        float4 c0 = __ldg(C + e);
+        float b[4] = {c0.x, c0.y, c0.z, c0.w};
+        int kb[4] = {0, 0, 0, 0};
+        if (MODE == OT_MIN) {
+            for (int k = 1; k < N; ++k) {
+                float4 ck = __ldg(C + (long long)k * mm4 + e);
+                min_step(ck.x, k, b[0], kb[0]);
+                min_step(ck.y, k, b[1], kb[1]);
+                min_step(ck.z, k, b[2], kb[2]);
+                min_step(ck.w, k, b[3], kb[3]);
+            }
+            G[e] = make_float4(b[0], b[1], b[2], b[3]);
+            if (ks) ks[e] = make_uchar4(kb[0], kb[1], kb[2], kb[3]);
+        } else {
+            // one pass, online soft-min: s = sum_k exp2((mn - C_k) * kappa) for the running minimum mn
+            float s[4] = {1.f, 1.f, 1.f, 1.f};
+            for (int k = 1; k < N; ++k) {
+                float4 ck = __ldg(C + (long long)k * mm4 + e);
+                softmin_step(ck.x, kappa, b[0], s[0]);
+                softmin_step(ck.y, kappa, b[1], s[1]);
+                softmin_step(ck.z, kappa, b[2], s[2]);
+                softmin_step(ck.w, kappa, b[3], s[3]);
+            }
+            const float inv = 1.0f / kappa;
+            G[e] = make_float4(b[0] - inv * lg2(s[0]), b[1] - inv * lg2(s[1]),
+                               b[2] - inv * lg2(s[2]), b[3] - inv * lg2(s[3]));
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(OT_BLOCK) fold_blocks_scalar(int N, long long mm, const float* __restrict__ C,
+                                                               float kappa, float* __restrict__ G,
+                                                               uint8_t* __restrict__ ks) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += stride) {
+        float best = __ldg(C + e);
+        int kb = 0;
+        if (MODE == OT_MIN) {
+            for (int k = 1; k < N; ++k) min_step(__ldg(C + (long long)k * mm + e), k, best, kb);
+            G[e] = best;
+            if (ks) ks[e] = (uint8_t)kb;
+        } else {
+            float s = 1.f;
+            for (int k = 1; k < N; ++k) softmin_step(__ldg(C + (long long)k * mm + e), kappa, best, s);
+            G[e] = best - lg2(s) / kappa;
+        }
+    }
+}
+
+// Points: C_k[i][j] = |x_i - R^k y_j|^2.  One thread per (i, j); the N
+// rotations of y_j are formed from the per-block (cos, sin) table in shared memory.
+template <int MODE>
+__global__ void __launch_bounds__(OT_BLOCK) fold_points(int m, int N, const float2* __restrict__ x,
+                                                        const float2* __restrict__ y, float kappa,
+                                                        float* __restrict__ G, uint8_t* __restrict__ ks) {
+    extern __shared__ float2 rot[];   // [N] (cos, sin) of 2*pi*k/N
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        float s, c;
+        sincospif(2.0f * (float)k / (float)N, &s, &c);
+        rot[k] = make_float2(c, s);
+    }
+    __syncthreads();
+    const long long mm = (long long)m * m;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += stride) {
+        const int i = (int)(e / m), j = (int)(e - (long long)i * m);
+        const float2 xi = __ldg(x + i), yj = __ldg(y + j);
+        float best = 0.f, sum = 1.f;
+        int kb = 0;
+        for (int k = 0; k < N; ++k) {
+            const float2 r = rot[k];
+            const float yx = r.x * yj.x - r.y * yj.y, yy = r.y * yj.x + r.x * yj.y;
+            const float dx = xi.x - yx, dy = xi.y - yy;
+            const float c = fmaf(dx, dx, dy * dy);
+            if (k == 0) best = c;
+            else if (MODE == OT_MIN) min_step(c, k, best, kb);
+            else softmin_step(c, kappa, best, sum);
+        }
+        if (MODE == OT_MIN) {
+            G[e] = best;
+            if (ks) ks[e] = (uint8_t)kb;
+        } else {
+            G[e] = best - lg2(sum) / kappa;
+        }
+    }
+}
+
+int grid_for(long long work, int sms) {
+    long long blocks = (work + OT_BLOCK - 1) / OT_BLOCK;
+    long long cap = (long long)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+int device_sms();
+
+}  // namespace cyc
+
+using namespace cyc;
+
+extern "C" int ot_fold_cost(int mode, int m, int N, const float* C_base, const float* x, const float* y,
+                            float eps, float* G, uint8_t* kstar, void* stream) {
+    if (m <= 0 || N <= 0 || G == nullptr) return OT_ERR_ARG;
+    if (mode != OT_MIN && mode != OT_SOFTMIN) return OT_ERR_ARG;
+    if (mode == OT_SOFTMIN && !(eps > 0.f)) return OT_ERR_ARG;
+    if (C_base == nullptr && (x == nullptr || y == nullptr)) return OT_ERR_ARG;
+    if (mode == OT_MIN && N > 255) return OT_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float kappa = mode == OT_SOFTMIN ? (float)(1.0 / ((double)eps * OT_LN2)) : 0.f;
+    const long long mm = (long long)m * m;
+    const int sms = device_sms();
+    if (sms <= 0) return OT_ERR_CUDA;
+    if (C_base) {
+        const bool vec = (mm % 4 == 0) && (((uintptr_t)C_base | (uintptr_t)G) % 16 == 0) &&
+                         (kstar == nullptr || ((uintptr_t)kstar % 4 == 0));
+        if (vec) {
+            const int grid = grid_for(mm / 4, sms);
+            if (mode == OT_MIN)
+                fold_blocks_vec4<OT_MIN><<<grid, OT_BLOCK, 0, st>>>(N, mm / 4, (const float4*)C_base, kappa,
+                                                                    (float4*)G, (uchar4*)kstar);
+            else
+                fold_blocks_vec4<OT_SOFTMIN><<<grid, OT_BLOCK, 0, st>>>(N, mm / 4, (const float4*)C_base, kappa,
+                                                                        (float4*)G, (uchar4*)kstar);
+        } else {
+            const int grid = grid_for(mm, sms);
+            if (mode == OT_MIN)
+                fold_blocks_scalar<OT_MIN><<<grid, OT_BLOCK, 0, st>>>(N, mm, C_base, kappa, G, kstar);
+            else
+                fold_blocks_scalar<OT_SOFTMIN><<<grid, OT_BLOCK, 0, st>>>(N, mm, C_base, kappa, G, kstar);
+        }
+    } else {
+        const int grid = grid_for(mm, sms);
+        const size_t shm = sizeof(float2) * (size_t)N;
+        if (mode == OT_MIN)
+            fold_points<OT_MIN><<<grid, OT_BLOCK, shm, st>>>(m, N, (const float2*)x, (const float2*)y, kappa, G,
+                                                             kstar);
+        else
+            fold_points<OT_SOFTMIN><<<grid, OT_BLOCK, shm, st>>>(m, N, (const float2*)x, (const float2*)y, kappa,
+                                                                 G, kstar);
+    }
+    return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}

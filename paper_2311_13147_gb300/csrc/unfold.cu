@@ -1,0 +1,136 @@
+// ot_unfold_plan: reconstruct the block-circulant plan from the reduced solution.
+//
+// LOT  (Theorem 1, Eq. optimal_solution_problem_CLOT): T_k[i][j] = S[i][j] if k == kstar[i][j] else 0.
+// EROT (Algorithm 2's reconstruction, Theorem 2 Eq. optimality_condition):
+//      T_k[i][j] = exp((w_i + z_j - C_k[i][j]) / eps).
+// Layout: compact first block row [N][m][m], or the dense n x n matrix with
+// T[r*m+i][c*m+j] = T_{(c-r) mod N}[i][j] (Lemma 1).
+//
+// Write-bound kernel.  A block covers a tile of TR rows x TC columns of one
+// block T_k; the potentials of the tile are split once into FP32 hi/lo pairs
+// in shared memory, so the per-entry work is FP32: 2^((wh_i + zh_j) - c_ij + (wl_i + zl_j)).
+// In dense mode each computed tile is stored N times (the N positions of
+// block k in the circulant), so every exponential is computed once.
+#include "common.cuh"
+
+namespace cyc {
+
+int device_sms();
+
+#define UT_R 16
+#define UT_C 256
+
+template <int MODE, bool POINTS>
+__global__ void __launch_bounds__(OT_BLOCK) unfold_kernel(int m, int N, const float* __restrict__ S,
+                                                          const double* __restrict__ w, const double* __restrict__ z,
+                                                          const float* __restrict__ C, const float2* __restrict__ x,
+                                                          const float2* __restrict__ y,
+                                                          const uint8_t* __restrict__ ks, float kappa, int dense,
+                                                          float* __restrict__ T) {
+    __shared__ float s_wh[UT_R], s_wl[UT_R], s_zh[UT_C], s_zl[UT_C];
+    __shared__ float2 s_rot;
+    const int tiles_r = (m + UT_R - 1) / UT_R, tiles_c = (m + UT_C - 1) / UT_C;
+    const long long ntiles = (long long)N * tiles_r * tiles_c;
+    const long long n = (long long)N * m;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = (int)(tile / ((long long)tiles_r * tiles_c));
+        const int rem = (int)(tile - (long long)k * tiles_r * tiles_c);
+        const int i0 = (rem / tiles_c) * UT_R, j0 = (rem % tiles_c) * UT_C;
+        __syncthreads();
+        if (MODE == OT_PLAN_EROT) {
+            if (threadIdx.x < UT_R) {
+                const int i = i0 + threadIdx.x;
+                float hi = 0.f, lo = 0.f;
+                if (i < m) split_f64(w[i] * (double)kappa, hi, lo);
+                s_wh[threadIdx.x] = hi;
+                s_wl[threadIdx.x] = lo;
+            }
+            for (int c = threadIdx.x; c < UT_C; c += OT_BLOCK) {
+                const int j = j0 + c;
+                float hi = 0.f, lo = 0.f;
+                if (j < m) split_f64(z[j] * (double)kappa, hi, lo);
+                s_zh[c] = hi;
+                s_zl[c] = lo;
+            }
+            if (POINTS && threadIdx.x == 0) {
+                float sn, cs;
+                sincospif(2.0f * (float)k / (float)N, &sn, &cs);
+                s_rot = make_float2(cs, sn);
+            }
+        }
+        __syncthreads();
+        const int c = threadIdx.x;   // one column per thread, UT_C == OT_BLOCK
+        const int j = j0 + c;
+        if (j >= m) continue;
+        float2 ykj = make_float2(0.f, 0.f);
+        if (POINTS) {
+            const float2 yj = y[j];
+            ykj = make_float2(s_rot.x * yj.x - s_rot.y * yj.y, s_rot.y * yj.x + s_rot.x * yj.y);
+        }
+        for (int r = 0; r < UT_R; ++r) {
+            const int i = i0 + r;
+            if (i >= m) break;
+            const long long e = (long long)i * m + j;
+            float v;
+            if (MODE == OT_PLAN_LOT) {
+                v = (ks[e] == k) ? S[e] : 0.f;
+            } else {
+                float cst;
+                if (POINTS) {
+                    const float2 xi = x[i];
+                    const float dx = xi.x - ykj.x, dy = xi.y - ykj.y;
+                    cst = fmaf(dx, dx, dy * dy);
+                } else {
+                    cst = __ldg(C + (long long)k * m * m + e);
+                }
+                const float arg = fmaf(cst, -kappa, s_wh[r] + s_zh[c]) + (s_wl[r] + s_zl[c]);
+                v = ex2(arg);
+            }
+            if (!dense) {
+                T[(long long)k * m * m + e] = v;
+            } else {
+                // block (rb, cb) with (cb - rb) mod N == k
+                for (int rb = 0; rb < N; ++rb) {
+                    const int cb = (rb + k) % N;
+                    T[((long long)rb * m + i) * n + (long long)cb * m + j] = v;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace cyc
+
+using namespace cyc;
+
+extern "C" int ot_unfold_plan(int mode, int m, int N, const void* S_or_w, const double* z, const float* C_base,
+                              const float* x, const float* y, const uint8_t* kstar, float eps, int dense, float* T,
+                              void* stream) {
+    if (m <= 0 || N <= 0 || !S_or_w || !T) return OT_ERR_ARG;
+    if (mode == OT_PLAN_LOT) {
+        if (!kstar || N > 255) return OT_ERR_ARG;
+    } else if (mode == OT_PLAN_EROT) {
+        if (!z || !(eps > 0.f)) return OT_ERR_ARG;
+        if (!C_base && (!x || !y)) return OT_ERR_ARG;
+    } else {
+        return OT_ERR_ARG;
+    }
+    const int sms = device_sms();
+    if (sms <= 0) return OT_ERR_CUDA;
+    const long long ntiles = (long long)N * ((m + UT_R - 1) / UT_R) * ((m + UT_C - 1) / UT_C);
+    long long grid = ntiles < (long long)sms * 8 ? ntiles : (long long)sms * 8;
+    if (grid < 1) grid = 1;
+    const float kappa = mode == OT_PLAN_EROT ? (float)(1.0 / ((double)eps * OT_LN2)) : 0.f;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == OT_PLAN_LOT)
+        unfold_kernel<OT_PLAN_LOT, false><<<(int)grid, OT_BLOCK, 0, st>>>(
+            m, N, (const float*)S_or_w, nullptr, nullptr, nullptr, nullptr, nullptr, kstar, 0.f, dense, T);
+    else if (C_base)
+        unfold_kernel<OT_PLAN_EROT, false><<<(int)grid, OT_BLOCK, 0, st>>>(
+            m, N, nullptr, (const double*)S_or_w, z, C_base, nullptr, nullptr, nullptr, kappa, dense, T);
+    else
+        unfold_kernel<OT_PLAN_EROT, true><<<(int)grid, OT_BLOCK, 0, st>>>(
+            m, N, nullptr, (const double*)S_or_w, z, nullptr, (const float2*)x, (const float2*)y, nullptr, kappa,
+            dense, T);
+    return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}

@@ -1,0 +1,278 @@
+"""Thin Python binding of ``libcyclicot.so`` (declared in ``include/cyclicot.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory (outputs, workspaces) and the
+current CUDA stream.  The functions carry the C names and follow the C
+argument order; outputs that the caller does not pass are allocated here as
+torch tensors on the inputs' device.
+
+There is no CPU fallback: if the library is missing or a tensor is not on a
+CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcyclicot.so")
+
+OT_OK = 0
+OT_ERR_ARG = 1
+OT_ERR_NOT_DIVISIBLE = 2
+OT_ERR_NOT_CONVERGED = 3
+OT_ERR_TIMEOUT = 4
+OT_ERR_NONFINITE = 5
+OT_ERR_CUDA = 6
+OT_ERR_WORKSPACE = 7
+OT_ERR_UNSUPPORTED = 8
+
+OT_MIN = 0
+OT_SOFTMIN = 1
+OT_PLAN_LOT = 0
+OT_PLAN_EROT = 1
+OT_ADJ_ENVELOPE = 0
+OT_ADJ_UNROLLED = 1
+OT_FP32_LOG = 0
+OT_BF16_KERNEL_POLISH = 1
+OT_OP_SINKHORN_REDUCED = 0
+OT_OP_SINKHORN_FULL = 1
+OT_OP_VALUE_AND_GRAD = 2
+OT_OP_UNROLLED = 3
+OT_DEBUG_WITHHOLD_ARRIVAL = 1
+
+EXPORTED = ("ot_version", "ot_status_string", "ot_workspace_bytes", "ot_fold_cost", "ot_sinkhorn_reduced",
+            "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad")
+
+
+class OTError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (code {code})")
+
+
+class ot_options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("tol_l1", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("precision", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("timeout_ns", ctypes.c_ulonglong), ("tile_override", ctypes.c_int),
+                ("debug_flags", ctypes.c_int)]
+
+
+class ot_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("marg_l1", ctypes.c_double),
+                ("marg_l2_col", ctypes.c_double), ("value", ctypes.c_double),
+                ("transport_cost", ctypes.c_double), ("marg_l1_col", ctypes.c_double),
+                ("reserved", ctypes.c_double * 2)]
+
+
+assert ctypes.sizeof(ot_result) == 64
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load the library once (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with paper_2311_13147_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.ot_version.restype = ctypes.c_char_p
+    L.ot_status_string.restype = ctypes.c_char_p
+    L.ot_status_string.argtypes = [ctypes.c_int]
+    L.ot_workspace_bytes.restype = ctypes.c_size_t
+    L.ot_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ot_options)]
+    L.ot_fold_cost.restype = ctypes.c_int
+    L.ot_fold_cost.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_float, _vp, _vp,
+                               _vp]
+    L.ot_sinkhorn_reduced.restype = ctypes.c_int
+    L.ot_sinkhorn_reduced.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(ot_options), _vp,
+                                      _vp, _vp, _vp, ctypes.c_size_t, _vp]
+    L.ot_sinkhorn_full.restype = ctypes.c_int
+    L.ot_sinkhorn_full.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ot_options), _vp, _vp,
+                                   _vp, _vp, ctypes.c_size_t, _vp]
+    L.ot_unfold_plan.restype = ctypes.c_int
+    L.ot_unfold_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                 ctypes.c_float, ctypes.c_int, _vp, _vp]
+    L.ot_value_and_grad.restype = ctypes.c_int
+    L.ot_value_and_grad.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    ctypes.c_float, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    ctypes.c_size_t, _vp]
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().ot_status_string(int(code)).decode()
+    except Exception:  # library missing: still give a readable message
+        return f"status {code}"
+
+
+def version() -> str:
+    return lib().ot_version().decode()
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("cyclicot takes CUDA tensors only (no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("cyclicot takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code != OT_OK:
+        raise OTError(code, where)
+
+
+def options(eps: float, tol: float = 1e-6, max_iter: int = 10000, check_every: int = 1,
+            warm_start: bool = False, timeout_ns: int = 0, precision: int = OT_FP32_LOG,
+            tile_override: int = 0, debug_flags: int = 0) -> ot_options:
+    return ot_options(float(eps), float(tol), int(max_iter), int(check_every), int(precision),
+                      int(bool(warm_start)), int(timeout_ns), int(tile_override), int(debug_flags))
+
+
+def new_result(device) -> torch.Tensor:
+    """A device-side ot_result record (64 bytes)."""
+    return torch.zeros(64, dtype=torch.uint8, device=device)
+
+
+def read_result(res: torch.Tensor) -> dict:
+    """Copy an ot_result record to the host (synchronises its stream)."""
+    raw = bytes(res.cpu().numpy().tobytes())
+    r = ot_result.from_buffer_copy(raw)
+    return {"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1, "marg_l2_col": r.marg_l2_col,
+            "value": r.value, "transport_cost": r.transport_cost, "marg_l1_col": r.marg_l1_col,
+            "mass": r.reserved[0]}
+
+
+def ot_workspace_bytes(op: int, m_or_n: int, N: int, opt: Optional[ot_options] = None) -> int:
+    return int(lib().ot_workspace_bytes(int(op), int(m_or_n), int(N),
+                                        ctypes.byref(opt) if opt is not None else None))
+
+
+def workspace(op: int, m_or_n: int, N: int, device, opt: Optional[ot_options] = None) -> torch.Tensor:
+    nbytes = ot_workspace_bytes(op, m_or_n, N, opt)
+    if nbytes <= 0:
+        raise OTError(OT_ERR_ARG, "ot_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------ entry points
+
+def ot_fold_cost(mode: int, m: int, N: int, C_base=None, x=None, y=None, eps: float = 0.0,
+                 G=None, kstar=None, stream=None):
+    dev = (C_base if C_base is not None else x).device
+    if G is None:
+        G = torch.empty((m, m), dtype=torch.float32, device=dev)
+    if mode == OT_MIN and kstar is None:
+        kstar = torch.empty((m, m), dtype=torch.uint8, device=dev)
+    code = lib().ot_fold_cost(int(mode), int(m), int(N), _ptr(C_base), _ptr(x), _ptr(y), float(eps), _ptr(G),
+                              _ptr(kstar), _stream(stream))
+    _check(code, "ot_fold_cost")
+    return G, kstar
+
+
+def ot_sinkhorn_reduced(m: int, N: int, a_base, b_base, G, opt: ot_options, w=None, z=None, out=None,
+                        ws=None, stream=None):
+    dev = G.device
+    w = torch.empty(m, dtype=torch.float64, device=dev) if w is None else w
+    z = torch.zeros(m, dtype=torch.float64, device=dev) if z is None else z
+    out = new_result(dev) if out is None else out
+    ws = workspace(OT_OP_SINKHORN_REDUCED, m, N, dev, opt) if ws is None else ws
+    code = lib().ot_sinkhorn_reduced(int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(G), ctypes.byref(opt),
+                                     _ptr(w), _ptr(z), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "ot_sinkhorn_reduced")
+    return w, z, out
+
+
+def ot_sinkhorn_full(n: int, a, b, C=None, X=None, Y=None, opt: ot_options = None, f=None, g=None, out=None,
+                     ws=None, stream=None):
+    dev = a.device
+    f = torch.empty(n, dtype=torch.float64, device=dev) if f is None else f
+    g = torch.zeros(n, dtype=torch.float64, device=dev) if g is None else g
+    out = new_result(dev) if out is None else out
+    ws = workspace(OT_OP_SINKHORN_FULL, n, 1, dev, opt) if ws is None else ws
+    code = lib().ot_sinkhorn_full(int(n), _ptr(a), _ptr(b), _ptr(C), _ptr(X), _ptr(Y), ctypes.byref(opt), _ptr(f),
+                                  _ptr(g), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "ot_sinkhorn_full")
+    return f, g, out
+
+
+def ot_unfold_plan(mode: int, m: int, N: int, S_or_w, z=None, C_base=None, x=None, y=None, kstar=None,
+                   eps: float = 0.0, dense: bool = False, T=None, stream=None):
+    dev = S_or_w.device
+    if T is None:
+        shape = (N * m, N * m) if dense else (N, m, m)
+        T = torch.empty(shape, dtype=torch.float32, device=dev)
+    code = lib().ot_unfold_plan(int(mode), int(m), int(N), _ptr(S_or_w), _ptr(z), _ptr(C_base), _ptr(x), _ptr(y),
+                                _ptr(kstar), float(eps), int(bool(dense)), _ptr(T), _stream(stream))
+    _check(code, "ot_unfold_plan")
+    return T
+
+
+def ot_value_and_grad(m: int, N: int, a_base, b_base, C_base=None, x=None, y=None, G=None, w=None, z=None,
+                      eps: float = 0.0, adjoint: int = OT_ADJ_ENVELOPE, unroll_iters: int = 0, out=None,
+                      d_a=None, d_b=None, d_C=None, d_x=None, d_y=None, ws=None, stream=None):
+    dev = a_base.device
+    out = new_result(dev) if out is None else out
+    if ws is None:
+        if adjoint == OT_ADJ_UNROLLED:
+            ws = workspace(OT_OP_UNROLLED, m, N, dev, options(eps, max_iter=unroll_iters))
+        else:
+            ws = workspace(OT_OP_VALUE_AND_GRAD, m, N, dev)
+    code = lib().ot_value_and_grad(int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(C_base), _ptr(x), _ptr(y),
+                                   _ptr(G), _ptr(w), _ptr(z), float(eps), int(adjoint), int(unroll_iters),
+                                   _ptr(out), _ptr(d_a), _ptr(d_b), _ptr(d_C), _ptr(d_x), _ptr(d_y), _ptr(ws),
+                                   ws.numel(), _stream(stream))
+    _check(code, "ot_value_and_grad")
+    return out
+
+
+# ------------------------------------------------------------------ convenience pipeline
+
+@dataclass
+class ReducedSolution:
+    w: torch.Tensor          # [m] float64, potentials for marginals of mass 1/N
+    z: torch.Tensor
+    G: torch.Tensor          # [m, m] folded cost
+    result: dict
+
+
+def cyclic_erot(a_base, b_base, eps: float, C_base=None, x=None, y=None, tol: float = 1e-6,
+                max_iter: int = 10000, check: bool = True) -> ReducedSolution:
+    """Fold (Eq. def_Kij) + cyclic Sinkhorn (Algorithm 2) through the C ABI."""
+    src = C_base if C_base is not None else x
+    N = C_base.shape[0] if C_base is not None else None
+    m = a_base.shape[0]
+    if N is None:
+        raise ValueError("pass N through C_base or use ot_fold_cost directly for points")
+    G, _ = ot_fold_cost(OT_SOFTMIN, m, N, C_base=C_base, x=x, y=y, eps=eps)
+    opt = options(eps, tol=tol, max_iter=max_iter)
+    w, z, out = ot_sinkhorn_reduced(m, N, a_base, b_base, G, opt)
+    res = read_result(out)
+    if check and res["status"] not in (OT_OK,):
+        raise OTError(res["status"], "ot_sinkhorn_reduced")
+    del src
+    return ReducedSolution(w=w, z=z, G=G, result=res)
+
+
+def eps_log_n(eps: float, N: int) -> float:
+    return float(eps) * math.log(N)

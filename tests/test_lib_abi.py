@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every symbol include/cyclicot.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cyclicot.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ot_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2311_13147_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("ot_fold_cost", "ot_sinkhorn_reduced", "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad",
+              "ot_workspace_bytes", "ot_status_string", "ot_version"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+
+
+def test_host_only_entry_points(libpath):
+    from paper_2311_13147_gb300 import cyclicot as cy
+    assert "sm_103a" in cy.version()
+    assert cy.status_string(cy.OT_ERR_TIMEOUT).startswith("OT_ERR_TIMEOUT")
+    assert cy.status_string(12345) == "unknown status"
+    assert ctypes.sizeof(cy.ot_result) == 64
+
+
+def test_binding_refuses_cpu_tensors(libpath):
+    import torch
+    from paper_2311_13147_gb300 import cyclicot as cy
+    C = torch.zeros((2, 4, 4))
+    with pytest.raises(ValueError):
+        cy.ot_fold_cost(cy.OT_MIN, 4, 2, C_base=C, G=torch.zeros((4, 4)), kstar=torch.zeros((4, 4), dtype=torch.uint8))
+
+
+def test_struct_layouts_match_header():
+    """ot_options / ot_result field order in the binding follows the header."""
+    from paper_2311_13147_gb300 import cyclicot as cy
+    text = open(HEADER).read()
+    for struct, cls in (("ot_options", cy.ot_options), ("ot_result", cy.ot_result)):
+        body = re.search(r"typedef struct \{([^{}]*)\} " + struct + ";", text).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"\b([a-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
+        assert [f[0] for f in cls._fields_] == fields
