@@ -86,13 +86,20 @@ typedef struct {
     int warm_start;                 /* 1: start from the g passed in (f is recomputed)     */
     unsigned long long timeout_ns;  /* limit of each device-side wait; 0 = 10 s            */
     int tile_override;              /* reserved, must be 0                                 */
-    int debug_flags;                /* fault injection for tests; 0 in normal use:
-                                       bit 0 (OT_DEBUG_WITHHOLD_ARRIVAL): block 0 never
-                                       arrives at the first grid barrier, so the other
-                                       blocks' bounded waits expire -> OT_ERR_TIMEOUT   */
+    int debug_flags;                /* 0 in normal use.
+                                       bit 0 (OT_DEBUG_WITHHOLD_ARRIVAL), fault injection:
+                                       block 0 never arrives at the first grid barrier,
+                                       so the other blocks' bounded waits expire and the
+                                       solve reports OT_ERR_TIMEOUT.
+                                       bit 1 (OT_DEBUG_TRACE), tracing: block 0 records
+                                       %globaltimer stamps (ns) per sweep t < 256 in the
+                                       last 16 KB of the workspace, 8 uint64 per sweep:
+                                       [0] sweep start, [1] row phase done, [2] after the
+                                       first grid barrier, [3] column phase done.        */
 } ot_options;
 
 #define OT_DEBUG_WITHHOLD_ARRIVAL 1
+#define OT_DEBUG_TRACE            2
 
 /* Device-written outcome of one solve.  64 bytes, naturally aligned. */
 typedef struct {

@@ -65,13 +65,23 @@ struct SkArgs {
     double* phi;                  // [2][M]  log2-unit row potentials (two buffers)
     float* fhi;                   // [2][M]  fl(phi)
     float* frf;                   // [2][M]  2^(phi - fhi)
-    double* gam;                  // [Ncol]
-    float* gc;                    // [Ncol]  fl(gamma)
-    float* cf;                    // [Ncol]  2^(gamma - gc)
+    double* gam;                  // [2][Ncol]  log2-unit column potentials (two buffers)
+    float* gc;                    // [2][Ncol]  fl(gamma)
+    float* cf;                    // [2][Ncol]  2^(gamma - gc)
     float* part;                  // [grid][pstride] column partials (fused kernel)
     double* l1part;               // [grid]
+    unsigned long long* trace;    // [kTraceSweeps][8] phase timestamps, or null
     int pstride;
 };
+
+// Buffers: the state after s iterations lives in phi[s & 1] and gam[s & 1].
+// Sweep t reads state t-1 and writes state t.
+
+#define OT_TRACE_SWEEPS 256
+__device__ __forceinline__ void trace_mark(const SkArgs& A, int t, int slot) {
+    if (A.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && t < OT_TRACE_SWEEPS)
+        A.trace[t * 8 + slot] = globaltimer();
+}
 
 __device__ __forceinline__ bool sum_ok(float s) { return s > 1e-30f && s < 1e30f; }
 
@@ -101,11 +111,11 @@ __device__ bool prologue_sums(const SkArgs& A, double& inv_sa, double& inv_sb, d
     return bad == 0;
 }
 
-__device__ __forceinline__ void store_col(const SkArgs& A, int j, double g) {
+__device__ __forceinline__ void store_col(const SkArgs& A, int buf, int j, double g) {
     float hi = (float)g;
-    A.gam[j] = g;
-    A.gc[j] = hi;
-    A.cf[j] = ex2((float)(g - (double)hi));
+    A.gam[buf * A.Ncol + j] = g;
+    A.gc[buf * A.Ncol + j] = hi;
+    A.cf[buf * A.Ncol + j] = ex2((float)(g - (double)hi));
 }
 
 __device__ __forceinline__ void store_row(const SkArgs& A, int buf, int i, double p) {
@@ -115,11 +125,27 @@ __device__ __forceinline__ void store_row(const SkArgs& A, int buf, int i, doubl
     A.frf[buf * A.M + i] = ex2((float)(p - (double)hi));
 }
 
-// Write the returned state (rows from buffer `buf`, current columns).
+// Write the returned state (rows and columns from buffer `buf`).
 __device__ void write_outputs(const SkArgs& A, int buf, int r_beg, int r_end, int c_beg, int c_end) {
     for (int i = r_beg + threadIdx.x; i < r_end; i += OT_BLOCK)
         A.f_out[i] = A.phi[buf * A.M + i] * A.unit + A.f_shift;
-    for (int j = c_beg + threadIdx.x; j < c_end; j += OT_BLOCK) A.g_out[j] = A.gam[j] * A.unit;
+    for (int j = c_beg + threadIdx.x; j < c_end; j += OT_BLOCK) A.g_out[j] = A.gam[buf * A.Ncol + j] * A.unit;
+}
+
+// Sum of the per-block L1 partials, all threads loading in parallel, fixed order.
+__device__ double total_l1(const SkArgs& A, double* s_dred) {
+    double v = 0.0;
+    for (int b2 = threadIdx.x; b2 < gridDim.x; b2 += OT_BLOCK) v += ((volatile double*)A.l1part)[b2];
+    return block_sum_d(v, s_dred);
+}
+
+// Stopping rule on the state after `done` iterations; returns the status or -1 to continue.
+__device__ __forceinline__ int stop_status(const SkArgs& A, int done, double L1) {
+    if (done < 1) return -1;
+    if (L1 != L1) return OT_ERR_NONFINITE;
+    if (done % A.check_every == 0 && L1 <= A.tol) return OT_OK;
+    if (done >= A.max_iter) return OT_ERR_NOT_CONVERGED;
+    return -1;
 }
 
 __device__ void write_result(const SkArgs& A, int iters, int status, double l1) {
@@ -141,9 +167,10 @@ __device__ void fail_exit(const SkArgs& A) {
     }
 }
 
-// Column update from a finished column sum R (true sum, column factor included).
+// Column update from a finished column sum R (true sum, column factor included):
+// gamma_new = gamma_old - log2(R / beta_j), read from buffer ob, written to nb.
 // Returns false if R is outside the safe range (caller falls back).
-__device__ __forceinline__ bool column_update(const SkArgs& A, int j, double R, double inv_sb) {
+__device__ __forceinline__ bool column_update(const SkArgs& A, int ob, int nb, int j, double R, double inv_sb) {
     if (R != R) {
         set_status(A.ctrl, OT_ERR_NONFINITE);
         return true;
@@ -151,7 +178,7 @@ __device__ __forceinline__ bool column_update(const SkArgs& A, int j, double R, 
     if (!(R > 1e-30 && R < 1e30)) return false;
     const double beta = (double)A.b[j] * inv_sb;
     const float d = lg2((float)(R / beta));
-    store_col(A, j, A.gam[j] - (double)d);
+    store_col(A, nb, j, A.gam[ob * A.Ncol + j] - (double)d);
     return true;
 }
 
@@ -159,6 +186,7 @@ __device__ __forceinline__ bool column_update(const SkArgs& A, int j, double R, 
 // from the new row potentials (buffer nb).  Whole block, one column.
 template <bool OTF>
 __device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, float* s_redf) {
+    // row potentials and the new column potential both live in buffer nb
     float mx = -INFINITY;
     const float* fh = A.fhi + nb * A.M;
     for (int i = threadIdx.x; i < A.M; i += OT_BLOCK) {
@@ -202,7 +230,7 @@ __device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, f
             set_status(A.ctrl, OT_ERR_NONFINITE);
         } else {
             // gamma_new = log2 beta - (m2 + log2 tot)
-            store_col(A, j, (double)lg2((float)beta) - (double)m2 - (double)lg2(tot));
+            store_col(A, nb, j, (double)lg2((float)beta) - (double)m2 - (double)lg2(tot));
         }
     }
     __syncthreads();
@@ -212,60 +240,84 @@ __device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, f
 // Fused single-read kernel (Ncol <= OT_BLOCK * CPT)
 // ---------------------------------------------------------------------------
 
+// Per-row values the band epilogue needs, loaded at the start of the band so
+// their latency hides behind the band's exponentials.
+struct RowPre {
+    float alpha, fhi, frf;
+    double phi;
+};
+
 template <int CPT, int R, bool SAFE>
 __device__ __forceinline__ void fused_band(const SkArgs& A, int rb, int nr, int cur, int nxt, double inv_sa,
                                            const float (&gcr)[CPT], const float (&cfr)[CPT], float (&e)[R][CPT],
                                            double& l1, float (*s_red)[R], float* s_F, float* s_u, int* s_bad) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // 1. exponents x = gamma_j - c_ij (+ phi_i when not SAFE)
+    RowPre pre = {1.f, 0.f, 1.f, 0.0};
+    if (tid < nr) {
+        const int row = rb + tid;
+        pre.alpha = (float)((double)A.a[row] * inv_sa);
+        if (!SAFE) {
+            pre.fhi = A.fhi[cur * A.M + row];
+            pre.frf = A.frf[cur * A.M + row];
+            pre.phi = A.phi[cur * A.M + row];
+        }
+    }
+    // 1. exponents x = gamma_j - c_ij (+ phi_i when not SAFE); invalid rows skipped (uniform branch)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const bool rv = r < nr;
-        const float* crow = A.C + (long long)(rb + (rv ? r : 0)) * A.ld;
-        const float F = (!SAFE && rv) ? A.fhi[cur * A.M + rb + r] : 0.f;
+        if (r < nr) {
+            const float* crow = A.C + (long long)(rb + r) * A.ld;
+            const float F = SAFE ? 0.f : A.fhi[cur * A.M + rb + r];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int j = tid + q * OT_BLOCK;
-            float x = -INFINITY;
-            if (rv && j < A.Ncol) x = fmaf(__ldg(crow + j), -A.kappa, gcr[q]) + F;
-            e[r][q] = x;
+            for (int q = 0; q < CPT; ++q) {
+                const int j = tid + q * OT_BLOCK;
+                e[r][q] = (j < A.Ncol) ? fmaf(__ldg(crow + j), -A.kappa, gcr[q]) + F : -INFINITY;
+            }
         }
     }
     if (SAFE) {
-        // per-row max, then shift
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            float mx = e[r][0];
+            if (r < nr) {
+                float mx = e[r][0];
 #pragma unroll
-            for (int q = 1; q < CPT; ++q) mx = fmaxf(mx, e[r][q]);
-            mx = warp_max(mx);
-            if (lane == 0) s_red[wid][r] = mx;
+                for (int q = 1; q < CPT; ++q) mx = fmaxf(mx, e[r][q]);
+                mx = warp_max(mx);
+                if (lane == 0) s_red[wid][r] = mx;
+            }
         }
         __syncthreads();
-        if (tid < R) {
+        if (tid < nr) {
             float mx = s_red[0][tid];
             for (int w = 1; w < OT_WARPS; ++w) mx = fmaxf(mx, s_red[w][tid]);
-            s_F[tid] = (tid < nr && mx > -INFINITY) ? -mx : 0.f;
+            s_F[tid] = (mx > -INFINITY) ? -mx : 0.f;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float F = s_F[r];
+            if (r < nr) {
+                const float F = s_F[r];
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) e[r][q] += F;
+                for (int q = 0; q < CPT; ++q) e[r][q] += F;
+            }
         }
     }
     // 2. e = 2^x * colfactor, row partial sums
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        float s = 0.f;
+        if (r < nr) {
+            float s = 0.f;
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            e[r][q] = ex2(e[r][q]) * cfr[q];
-            s += e[r][q];
+            for (int q = 0; q < CPT; ++q) {
+                e[r][q] = ex2(e[r][q]) * cfr[q];
+                s += e[r][q];
+            }
+            s = warp_sum(s);
+            if (lane == 0) s_red[wid][r] = s;
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) e[r][q] = 0.f;
         }
-        s = warp_sum(s);
-        if (lane == 0) s_red[wid][r] = s;
     }
     __syncthreads();
     // 3. row epilogue: one thread per row
@@ -274,24 +326,18 @@ __device__ __forceinline__ void fused_band(const SkArgs& A, int rb, int nr, int 
         if (tid < nr) {
             const int row = rb + tid;
             float S = 0.f;
+#pragma unroll
             for (int w = 0; w < OT_WARPS; ++w) S += s_red[w][tid];
-            const double alpha64 = (double)A.a[row] * inv_sa;
-            const float alpha = (float)alpha64;
-            bool ok = true;
+            const float alpha = pre.alpha;
             double pnew;
             if (!SAFE) {
-                const float rf = A.frf[cur * A.M + row];
                 // L1 term of the current state: |S * 2^lo - alpha|
-                l1 += fabs((double)fmaf(S, rf - 1.0f, S - alpha));
-                ok = sum_ok(S);
-                const double pold = A.phi[cur * A.M + row];
-                const double lo = pold - (double)A.fhi[cur * A.M + row];
-                pnew = pold - lo - (double)lg2(S / alpha);
+                l1 += fabs((double)fmaf(S, pre.frf - 1.0f, S - alpha));
+                pnew = (double)pre.fhi - (double)lg2(S / alpha);
             } else {
-                ok = sum_ok(S);
                 pnew = (double)s_F[tid] - (double)lg2(S / alpha);
             }
-            if (ok) {
+            if (sum_ok(S)) {
                 store_row(A, nxt, row, pnew);
                 u = alpha / S;
             } else {
@@ -311,7 +357,6 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
     __shared__ int s_bad;
     __shared__ double s_dred[OT_WARPS];
     __shared__ float s_redf[OT_WARPS];
-    __shared__ double s_l1tot;
     __shared__ int s_flag_cols[64];
     __shared__ int s_nflag;
 
@@ -325,8 +370,8 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
         if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0);
         return;
     }
-    for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) store_col(A, j, A.warm ? A.g_out[j] / A.unit : 0.0);
-    if (tid == 0) s_bad = 0;
+    for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) store_col(A, 0, j, A.warm ? A.g_out[j] / A.unit : 0.0);
+    if (tid == 0) { s_bad = 0; s_nflag = 0; }
     if ((A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
         withhold_arrival(A.ctrl, A.timeout_ns);
         fail_exit(A);
@@ -336,13 +381,14 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
 
     for (int t = 1;; ++t) {
         const int cur = (t - 1) & 1, nxt = cur ^ 1;
+        trace_mark(A, t, 0);
         float gcr[CPT], cfr[CPT], acc[CPT];
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             const int j = tid + q * OT_BLOCK;
             const bool v = j < A.Ncol;
-            gcr[q] = v ? A.gc[j] : 0.f;
-            cfr[q] = v ? A.cf[j] : 0.f;
+            gcr[q] = v ? A.gc[cur * A.Ncol + j] : 0.f;
+            cfr[q] = v ? A.cf[cur * A.Ncol + j] : 0.f;
             acc[q] = 0.f;
         }
         double l1 = 0.0;
@@ -367,11 +413,12 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const float u = s_u[r];
+                if (r < nr) {
+                    const float u = s_u[r];
 #pragma unroll
-                for (int q = 0; q < CPT; ++q) acc[q] = fmaf(u, e[r][q], acc[q]);
+                    for (int q = 0; q < CPT; ++q) acc[q] = fmaf(u, e[r][q], acc[q]);
+                }
             }
-            __syncthreads();
         }
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
@@ -380,48 +427,36 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
         }
         l1 = block_sum_d(l1, s_dred);
         if (tid == 0) A.l1part[B] = l1;
+        trace_mark(A, t, 1);
         if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
+        trace_mark(A, t, 2);
 
-        // ---- stopping rule on the state after iteration t-1
-        if (tid == 0) {
-            double s = 0.0;
-            for (int b2 = 0; b2 < G; ++b2) s += ((volatile double*)A.l1part)[b2];
-            s_l1tot = s;
-        }
-        __syncthreads();
-        const double L1 = s_l1tot;
-        const int done = t - 1;
-        if (done >= 1) {
-            int st = -1;
-            if (L1 != L1) st = OT_ERR_NONFINITE;
-            else if (done % A.check_every == 0 && L1 <= A.tol) st = OT_OK;
-            else if (done >= A.max_iter) st = OT_ERR_NOT_CONVERGED;
-            if (st >= 0) {
-                write_outputs(A, cur, r_beg, r_end, c_beg, c_end);
-                if (B == 0) write_result(A, done, st, L1);
-                return;
-            }
-        }
-
-        // ---- column phase: reduce partials for owned columns (one warp per column)
-        if (tid == 0) s_nflag = 0;
-        __syncthreads();
+        // ---- column phase for owned columns (one warp per column), writes buffer nxt
         for (int j = c_beg + wid; j < c_end; j += OT_WARPS) {
             double s = 0.0;
             for (int b2 = lane; b2 < G; b2 += 32) s += (double)A.part[(long long)b2 * A.pstride + j];
             s = warp_sum(s);
             if (lane == 0) {
-                const double Rj = s * (double)1.0;   // column factor already inside e
-                if (!column_update(A, j, Rj, inv_sb)) {
+                if (!column_update(A, cur, nxt, j, s, inv_sb)) {
                     const int k = atomicAdd(&s_nflag, 1);
                     if (k < 64) s_flag_cols[k] = j;
                     else set_status(A.ctrl, OT_ERR_NONFINITE);
                 }
             }
         }
-        __syncthreads();
+        // ---- stopping rule on the state after iteration t-1 (overlaps the column phase)
+        const double L1 = total_l1(A, s_dred);
+        const int st = stop_status(A, t - 1, L1);
+        if (st >= 0) {
+            write_outputs(A, cur, r_beg, r_end, c_beg, c_end);
+            if (B == 0) write_result(A, t - 1, st, L1);
+            return;
+        }
         const int nflag = min(s_nflag, 64);
+        __syncthreads();
+        if (tid == 0) s_nflag = 0;
         for (int k = 0; k < nflag; ++k) column_fallback<false>(A, s_flag_cols[k], nxt, inv_sb, s_redf);
+        trace_mark(A, t, 3);
         if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
     }
 }
@@ -432,29 +467,31 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
 
 #define WR 8   // rows per band in the two-pass row phase
 
-template <bool OTF>
-__device__ __forceinline__ float cost_at(const SkArgs& A, int i, int j, float2 xi) {
-    if (OTF) {
-        const float2 yj = __ldg(A.Y + j);
-        const float dx = xi.x - yj.x, dy = xi.y - yj.y;
-        return fmaf(dx, dx, dy * dy);
-    } else {
-        return __ldg(A.C + (long long)i * A.ld + j);
-    }
-}
-
 // Row phase for a band of up to WR rows: S_r = sum_j 2^(F_r + gamma_j - c_rj) * cf_j.
 // SAFE: F_r = -max_j(gamma_j - c_rj) (extra pass).  Writes phi_new; adds L1.
 template <bool OTF, bool SAFE>
 __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int nxt, double inv_sa, double& l1,
                                  float (*s_red)[WR], float* s_F, int* s_bad) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float* gcp = A.gc + cur * A.Ncol;
+    const float* cfp = A.cf + cur * A.Ncol;
+    RowPre pre = {1.f, 0.f, 1.f, 0.0};
+    if (tid < nr) {
+        const int row = rb + tid;
+        pre.alpha = (float)((double)A.a[row] * inv_sa);
+        if (!SAFE) {
+            pre.fhi = A.fhi[cur * A.M + row];
+            pre.frf = A.frf[cur * A.M + row];
+        }
+    }
     float F[WR];
     float2 xr[WR];
+    const float* crow[WR];
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
         const int row = rb + (r < nr ? r : 0);
         xr[r] = OTF ? __ldg(A.X + row) : make_float2(0.f, 0.f);
+        crow[r] = OTF ? nullptr : A.C + (long long)row * A.ld;
         F[r] = (!SAFE && r < nr) ? A.fhi[cur * A.M + row] : 0.f;
     }
     if (SAFE) {
@@ -462,10 +499,22 @@ __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int n
 #pragma unroll
         for (int r = 0; r < WR; ++r) mx[r] = -INFINITY;
         for (int j = tid; j < A.Ncol; j += OT_BLOCK) {
-            const float g = A.gc[j];
+            const float g = gcp[j];
+            float2 yj = make_float2(0.f, 0.f);
+            if (OTF) yj = __ldg(A.Y + j);
 #pragma unroll
-            for (int r = 0; r < WR; ++r)
-                if (r < nr) mx[r] = fmaxf(mx[r], fmaf(cost_at<OTF>(A, rb + r, j, xr[r]), -A.kappa, g));
+            for (int r = 0; r < WR; ++r) {
+                if (r < nr) {
+                    float c;
+                    if (OTF) {
+                        const float dx = xr[r].x - yj.x, dy = xr[r].y - yj.y;
+                        c = fmaf(dx, dx, dy * dy);
+                    } else {
+                        c = __ldg(crow[r] + j);
+                    }
+                    mx[r] = fmaxf(mx[r], fmaf(c, -A.kappa, g));
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < WR; ++r) {
@@ -486,10 +535,22 @@ __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int n
 #pragma unroll
     for (int r = 0; r < WR; ++r) s[r] = 0.f;
     for (int j = tid; j < A.Ncol; j += OT_BLOCK) {
-        const float g = A.gc[j], c = A.cf[j];
+        const float g = gcp[j], cfj = cfp[j];
+        float2 yj = make_float2(0.f, 0.f);
+        if (OTF) yj = __ldg(A.Y + j);
 #pragma unroll
-        for (int r = 0; r < WR; ++r)
-            if (r < nr) s[r] += ex2(fmaf(cost_at<OTF>(A, rb + r, j, xr[r]), -A.kappa, g) + F[r]) * c;
+        for (int r = 0; r < WR; ++r) {
+            if (r < nr) {
+                float c;
+                if (OTF) {
+                    const float dx = xr[r].x - yj.x, dy = xr[r].y - yj.y;
+                    c = fmaf(dx, dx, dy * dy);
+                } else {
+                    c = __ldg(crow[r] + j);
+                }
+                s[r] += ex2(fmaf(c, -A.kappa, g) + F[r]) * cfj;
+            }
+        }
     }
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
@@ -501,18 +562,15 @@ __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int n
         const int row = rb + tid;
         float S = 0.f;
         for (int w = 0; w < OT_WARPS; ++w) S += s_red[w][tid];
-        const float alpha = (float)((double)A.a[row] * inv_sa);
+        const float alpha = pre.alpha;
         double pnew;
-        bool ok = sum_ok(S);
         if (!SAFE) {
-            const float rf = A.frf[cur * A.M + row];
-            l1 += fabs((double)fmaf(S, rf - 1.0f, S - alpha));
-            const double pold = A.phi[cur * A.M + row];
-            pnew = pold - (pold - (double)A.fhi[cur * A.M + row]) - (double)lg2(S / alpha);
+            l1 += fabs((double)fmaf(S, pre.frf - 1.0f, S - alpha));
+            pnew = (double)pre.fhi - (double)lg2(S / alpha);
         } else {
             pnew = (double)s_F[tid] - (double)lg2(S / alpha);
         }
-        if (ok) store_row(A, nxt, row, pnew);
+        if (sum_ok(S)) store_row(A, nxt, row, pnew);
         else *s_bad = 1;
     }
     __syncthreads();
@@ -525,8 +583,8 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
     __shared__ int s_bad;
     __shared__ double s_dred[OT_WARPS];
     __shared__ float s_redf[OT_WARPS];
-    __shared__ double s_l1tot;
-    __shared__ double s_col[OT_WARPS][32];
+    __shared__ float s_col[OT_WARPS][32];
+    __shared__ int s_flag[32];
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int B = blockIdx.x, G = gridDim.x;
@@ -541,7 +599,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
         if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0);
         return;
     }
-    for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) store_col(A, j, A.warm ? A.g_out[j] / A.unit : 0.0);
+    for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) store_col(A, 0, j, A.warm ? A.g_out[j] / A.unit : 0.0);
     if (tid == 0) s_bad = 0;
     if ((A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
         withhold_arrival(A.ctrl, A.timeout_ns);
@@ -552,6 +610,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
 
     for (int t = 1;; ++t) {
         const int cur = (t - 1) & 1, nxt = cur ^ 1;
+        trace_mark(A, t, 0);
         double l1 = 0.0;
         for (int rb = r_beg; rb < r_end; rb += WR) {
             const int nr = min(WR, r_end - rb);
@@ -570,35 +629,25 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
         }
         l1 = block_sum_d(l1, s_dred);
         if (tid == 0) A.l1part[B] = l1;
+        trace_mark(A, t, 1);
         if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
+        trace_mark(A, t, 2);
 
-        if (tid == 0) {
-            double s = 0.0;
-            for (int b2 = 0; b2 < G; ++b2) s += ((volatile double*)A.l1part)[b2];
-            s_l1tot = s;
-        }
-        __syncthreads();
-        const double L1 = s_l1tot;
-        const int done = t - 1;
-        if (done >= 1) {
-            int st = -1;
-            if (L1 != L1) st = OT_ERR_NONFINITE;
-            else if (done % A.check_every == 0 && L1 <= A.tol) st = OT_OK;
-            else if (done >= A.max_iter) st = OT_ERR_NOT_CONVERGED;
-            if (st >= 0) {
-                write_outputs(A, cur, r_beg, r_end, c_beg, c_end);
-                if (B == 0) write_result(A, done, st, L1);
-                return;
-            }
+        const double L1 = total_l1(A, s_dred);
+        const int st = stop_status(A, t - 1, L1);
+        if (st >= 0) {
+            write_outputs(A, cur, r_beg, r_end, c_beg, c_end);
+            if (B == 0) write_result(A, t - 1, st, L1);
+            return;
         }
 
-        // ---- column pass: lane <-> column, warps split the rows
+        // ---- column pass: lane <-> column, warps split the rows; writes buffer nxt
         const float* fh = A.fhi + nxt * A.M;
         const float* fr = A.frf + nxt * A.M;
         for (int c0 = c_beg; c0 < c_end; c0 += 32) {
             const int j = c0 + lane;
             const bool jv = j < c_end;
-            const float g = jv ? A.gc[j] : 0.f;
+            const float g = jv ? A.gc[cur * A.Ncol + j] : 0.f;
             const float2 yj = (OTF && jv) ? __ldg(A.Y + j) : make_float2(0.f, 0.f);
             float s = 0.f;
             if (jv) {
@@ -614,34 +663,23 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
                     s += ex2(fmaf(c, -A.kappa, fh[i]) + g) * fr[i];
                 }
             }
-            s_col[wid][lane] = (double)s;
+            s_col[wid][lane] = s;
             __syncthreads();
-            int bad = 0;
-            if (wid == 0 && jv) {
-                double R = 0.0;
-                for (int w = 0; w < OT_WARPS; ++w) R += s_col[w][lane];
-                R *= (double)A.cf[j];
-                bad = !column_update(A, j, R, inv_sb);
-            }
-            bad = __syncthreads_or(bad);
-            if (bad) {
-                // rare: redo the flagged columns of this chunk with an explicit max
-                for (int l = 0; l < 32 && c0 + l < c_end; ++l) {
-                    __shared__ int s_fl;
-                    if (tid == 0) s_fl = 0;
-                    __syncthreads();
-                    if (wid == 0 && lane == l) {
-                        double R = 0.0;
-                        for (int w = 0; w < OT_WARPS; ++w) R += s_col[w][lane];
-                        R *= (double)A.cf[c0 + l];
-                        s_fl = !(R > 1e-30 && R < 1e30) && (R == R);
-                    }
-                    __syncthreads();
-                    if (s_fl) column_fallback<OTF>(A, c0 + l, nxt, inv_sb, s_redf);
+            if (wid == 0) {
+                int bad = 0;
+                if (jv) {
+                    double R = 0.0;
+                    for (int w = 0; w < OT_WARPS; ++w) R += (double)s_col[w][lane];
+                    R *= (double)A.cf[cur * A.Ncol + j];
+                    bad = !column_update(A, cur, nxt, j, R, inv_sb);
                 }
+                s_flag[lane] = bad;
             }
             __syncthreads();
+            for (int l = 0; l < 32; ++l)
+                if (s_flag[l]) column_fallback<OTF>(A, c0 + l, nxt, inv_sb, s_redf);
         }
+        trace_mark(A, t, 3);
         if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
     }
 }
@@ -653,7 +691,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t ctrl, phi, fhi, frf, gam, gc, cf, part, l1part, total;
+    size_t ctrl, phi, fhi, frf, gam, gc, cf, part, l1part, trace, total;
     int pstride;
 };
 
@@ -665,11 +703,12 @@ static WsLayout ws_layout(int M, int Ncol, int grid, bool fused) {
     L.phi = o; o = align256(o + sizeof(double) * 2 * (size_t)M);
     L.fhi = o; o = align256(o + sizeof(float) * 2 * (size_t)M);
     L.frf = o; o = align256(o + sizeof(float) * 2 * (size_t)M);
-    L.gam = o; o = align256(o + sizeof(double) * (size_t)Ncol);
-    L.gc = o; o = align256(o + sizeof(float) * (size_t)Ncol);
-    L.cf = o; o = align256(o + sizeof(float) * (size_t)Ncol);
+    L.gam = o; o = align256(o + sizeof(double) * 2 * (size_t)Ncol);
+    L.gc = o; o = align256(o + sizeof(float) * 2 * (size_t)Ncol);
+    L.cf = o; o = align256(o + sizeof(float) * 2 * (size_t)Ncol);
     L.part = o; o = align256(o + (fused ? sizeof(float) * (size_t)grid * L.pstride : 0));
     L.l1part = o; o = align256(o + sizeof(double) * (size_t)grid);
+    L.trace = o; o = align256(o + sizeof(unsigned long long) * 8 * OT_TRACE_SWEEPS);
     L.total = o;
     return L;
 }
@@ -729,6 +768,7 @@ int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
     A.cf = (float*)(w + L.cf);
     A.part = (float*)(w + L.part);
     A.l1part = (double*)(w + L.l1part);
+    A.trace = (A.debug_flags & OT_DEBUG_TRACE) ? (unsigned long long*)(w + L.trace) : nullptr;
     A.pstride = L.pstride;
     if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return OT_ERR_CUDA;
     if (!fused) {

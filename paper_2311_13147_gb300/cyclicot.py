@@ -45,6 +45,7 @@ OT_OP_SINKHORN_FULL = 1
 OT_OP_VALUE_AND_GRAD = 2
 OT_OP_UNROLLED = 3
 OT_DEBUG_WITHHOLD_ARRIVAL = 1
+OT_DEBUG_TRACE = 2
 
 EXPORTED = ("ot_version", "ot_status_string", "ot_workspace_bytes", "ot_fold_cost", "ot_sinkhorn_reduced",
             "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad")
@@ -276,3 +277,16 @@ def cyclic_erot(a_base, b_base, eps: float, C_base=None, x=None, y=None, tol: fl
 
 def eps_log_n(eps: float, N: int) -> float:
     return float(eps) * math.log(N)
+
+
+def read_trace(ws: torch.Tensor) -> "np.ndarray":
+    """Per-sweep phase timestamps (ns) written with debug_flags & OT_DEBUG_TRACE.
+
+    The trace occupies the last 16 KB of a solver workspace: 256 sweeps x 8
+    uint64 slots ([0] sweep start, [1] row phase done, [2] after the first
+    grid barrier, [3] column phase done).  Rows never written are zero.
+    """
+    import numpy as np
+    torch.cuda.synchronize()
+    raw = ws[-256 * 8 * 8:].cpu().numpy().tobytes()
+    return np.frombuffer(raw, dtype=np.uint64).reshape(256, 8).astype(np.int64)
