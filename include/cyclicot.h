@@ -95,11 +95,15 @@ typedef struct {
                                        %globaltimer stamps (ns) per sweep t < 256 in the
                                        last 16 KB of the workspace, 8 uint64 per sweep:
                                        [0] sweep start, [1] row phase done, [2] after the
-                                       first grid barrier, [3] column phase done.        */
+                                       first grid barrier, [3] column phase done.
+                                       bit 2 (OT_DEBUG_NO_CLUSTER): do not use the
+                                       one-barrier-per-sweep (bulk reduce-add) solver;
+                                       use the two-barrier one (comparison runs).        */
 } ot_options;
 
 #define OT_DEBUG_WITHHOLD_ARRIVAL 1
 #define OT_DEBUG_TRACE            2
+#define OT_DEBUG_NO_CLUSTER       4
 
 /* Device-written outcome of one solve.  64 bytes, naturally aligned. */
 typedef struct {

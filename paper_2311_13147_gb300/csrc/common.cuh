@@ -54,46 +54,102 @@ __device__ __forceinline__ int ld_volatile_int(const int* p) {
 // Control block at the start of every persistent-kernel workspace.  The host
 // zeroes it (cudaMemsetAsync) before each launch.
 struct Ctrl {
-    unsigned count;      // arrivals at the current barrier
-    unsigned gen;        // barrier generation
+    unsigned count;      // monotonic barrier arrival counter
+    unsigned gen;        // unused (kept for layout)
     int status;          // first device-side error (OT_ERR_*), 0 if none
     int flag;            // kernel-specific shared flag
     unsigned long long pad[6];
 };
 static_assert(sizeof(Ctrl) == 64, "Ctrl must stay 64 bytes");
 
-// Grid-wide barrier for a cooperative launch.  Returns false (in every thread
-// of the block) if the wait expired or another block already recorded an
-// error; the caller must then leave the kernel.
-__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned long long timeout_ns) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch.  `epoch` counts the barriers this
+// block has passed (start at 0, the caller keeps it): arrivals accumulate on a
+// monotonic counter and barrier k completes when it reaches nblocks * (k + 1).
+// Returns false (in every thread of the block) if the wait expired or another
+// block already recorded an error; the caller must then leave the kernel.
+__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned long long timeout_ns,
+                                          unsigned& epoch) {
     __shared__ int s_ok;
     __syncthreads();
+    epoch += 1;
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        unsigned g = ld_acquire(&c->gen);
-        unsigned old = atomicAdd(&c->count, 1u);
-        if (old == nblocks - 1) {
-            c->count = 0;
-            __threadfence();
-            st_release(&c->gen, g + 1);
-        } else {
-            unsigned long long t0 = globaltimer();
-            while (ld_acquire(&c->gen) == g) {
+        const unsigned target = nblocks * epoch;
+        red_release_add(&c->count, 1u);
+        if ((int)(ld_acquire(&c->count) - target) < 0) {
+            const unsigned long long t0 = globaltimer();
+            while ((int)(ld_acquire(&c->count) - target) < 0) {
                 if (globaltimer() - t0 > timeout_ns) {
                     atomicCAS(&c->status, 0, OT_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(20);
             }
         }
-        __threadfence();
         if (ld_volatile_int(&c->status) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// ---- mbarrier + bulk async copy (TMA 1D) helpers ------------------------------
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> shared, completion counted on `bar` (bytes, dst, src 16-byte multiples/aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > timeout_ns) return false;
+    }
+    return true;
 }
 
 __device__ __forceinline__ void set_status(Ctrl* c, int st) { atomicCAS(&c->status, 0, st); }
@@ -114,6 +170,91 @@ __device__ __forceinline__ bool withhold_arrival(Ctrl* c, unsigned long long tim
     }
     __syncthreads();
     return false;
+}
+
+// ---- thread-block cluster helpers (distributed shared memory) ------------------
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_nctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared::cluster address of the same variable in CTA `rank` of this cluster.
+__device__ __forceinline__ unsigned mapa_rank(const void* p, unsigned rank) {
+    unsigned out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_addr(p)), "r"(rank));
+    return out;
+}
+
+// Distributed-shared-memory loads.  Not volatile: the cluster barrier that
+// precedes every use orders them, and independent loads may then be batched.
+__device__ __forceinline__ float ld_dsmem_f32(unsigned caddr) {
+    float v;
+    asm("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(caddr));
+    return v;
+}
+
+__device__ __forceinline__ double ld_dsmem_f64(unsigned caddr) {
+    double v;
+    asm("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(caddr));
+    return v;
+}
+
+// Hardware cluster barrier: used once, right after the mbarriers are initialised
+// (no block can have left the kernel at that point).
+__device__ __forceinline__ void cluster_barrier_hw() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_remote_arrive(unsigned caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Cluster-wide barrier with a bounded wait: every block arrives on every
+// block's `cbar` (initialised with the cluster size), then waits on its own.
+// `phase` counts the cluster barriers this block has passed.  Returns false
+// (all threads) if the wait expired; OT_ERR_TIMEOUT is then recorded in `c`.
+__device__ __forceinline__ bool cluster_sync_bounded(unsigned long long* cbar, unsigned& phase, unsigned ncta,
+                                                     Ctrl* c, unsigned long long timeout_ns) {
+    __shared__ int s_cok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (unsigned r = 0; r < ncta; ++r) mbar_remote_arrive(mapa_rank(cbar, r));
+        int ok = 1;
+        if (!mbar_try_wait_cluster(cbar, phase & 1)) {
+            const unsigned long long t0 = globaltimer();
+            while (!mbar_try_wait_cluster(cbar, phase & 1)) {
+                if (globaltimer() - t0 > timeout_ns) {
+                    atomicCAS(&c->status, 0, OT_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_cok = ok;
+    }
+    phase += 1;
+    __syncthreads();
+    return s_cok != 0;
 }
 
 template <typename T>

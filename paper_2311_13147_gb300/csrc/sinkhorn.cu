@@ -13,26 +13,36 @@
 // row pass computes e_ij = 2^(phi_i + gamma_j - c_ij) with the OLD phi, whose
 // row sum S_i is the current row marginal (so the stopping rule is fused into
 // the pass) and whose terms are <= 1 after a column update (no overflow, no
-// running max).  Rows whose sum leaves [1e-30, 1e30] (first sweep, far warm
-// starts) are redone with an explicit max shift.
+// running max).  The first sweep, and any row whose sum leaves [1e-30, 1e30]
+// (far warm starts), uses an explicit max shift instead.
 //
-// Fused single-read sweep (narrow problems, Ncol <= 4096): a block owns a
-// contiguous row range and keeps a band of R rows x all columns in registers.
-// After the band's row sums give phi_new, the column contributions of the same
-// entries are u_i * e_ij with u_i = alpha_i / S_i -- the row pass's
-// exponentials reused, because 2^(phi_new_i + gamma_j - c_ij) = e_ij * alpha_i / S_i.
-// One cost read and ONE exp2 per entry per sweep.  Per-block column partials
-// go to the workspace; after a grid barrier the column owners reduce them in
-// a fixed order (FP64) and update gamma.  Second barrier, next sweep.
+// Fused single-read sweep (stored cost, Ncol <= 4096, Ncol % 4 == 0): a block
+// owns a contiguous row range.  Bands of R rows are copied into shared memory
+// by bulk asynchronous copies (TMA 1D, mbarrier completion): once for the whole
+// solve when the block's rows fit ("resident", e.g. the 1024 x 1024 folded
+// cost), else streamed through two stages so the next band is in flight while
+// the current one is computed.  After a band's row sums give phi_new, the
+// column contributions of the same entries are u_i * e_ij with u_i = alpha_i/S_i
+// -- the row pass's exponentials reused, since
+// 2^(phi_new_i + gamma_j - c_ij) = e_ij * alpha_i / S_i.  One cost read and ONE
+// exp2 per entry per sweep.  Per-block column partials go to the workspace;
+// after a grid barrier the column owners reduce them (compensated FP32 per
+// warp, FP64 across warps, fixed order) and update gamma; a second barrier
+// publishes gamma.
 //
-// Two-pass sweep (wide or on-the-fly costs): row pass then column pass, each
-// a full sweep over the cost (two exp2 per entry), no partials.
+// Two-pass sweep (wide, odd-sized or on-the-fly costs): a row pass then a
+// column pass over the cost (two exp2 per entry, no partials); the column pass
+// hands out 32-column chunks through an atomic work queue.
 //
-// Potentials are carried in FP64 (2 values per row/column per sweep) and
-// split into FP32 hi + a FP32 factor 2^lo for the inner loops, which are pure
-// FP32: an FP32 potential alone would bias every plan row by up to
-// ulp(phi)/2 relative, above a 1e-6 marginal target when |f|/eps ~ 100.
+// Potentials are carried in FP64 (a few values per row/column per sweep) and
+// split into an FP32 hi part plus an FP32 factor 2^lo for the inner loops,
+// which are pure FP32: an FP32 potential alone would bias every plan row by up
+// to ulp(phi)/2 relative, above a 1e-6 marginal target when |f|/eps ~ 100.
+// Each block keeps the potentials of the rows (and, in the fused kernel, the
+// columns) it owns in shared memory; global copies exist only to share column
+// potentials between blocks, for the rare column fallback and for the output.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -70,11 +80,17 @@ struct SkArgs {
     float* cf;                    // [2][Ncol]  2^(gamma - gc)
     float* part;                  // [grid][pstride] column partials (fused kernel)
     double* l1part;               // [grid]
-    unsigned long long* trace;    // [kTraceSweeps][8] phase timestamps, or null
+    unsigned* queue;              // [2] column-chunk queue counters (two-pass kernel)
+    double* acc;                  // [3][vstride] column sums + L1 (bulk-reduce kernel)
+    int vstride;
+    unsigned long long* trace;    // [OT_TRACE_SWEEPS][8] phase timestamps, or null
     int pstride;
+    int resident;                 // fused kernel: all of a block's rows stay in shared memory
+    int rows_max;                 // max rows owned by a block
+    int cols_max;                 // max columns owned by a block (fused kernel)
 };
 
-// Buffers: the state after s iterations lives in phi[s & 1] and gam[s & 1].
+// Buffers: the state after s iterations lives in buffer s & 1 (phi, gamma).
 // Sweep t reads state t-1 and writes state t.
 
 #define OT_TRACE_SWEEPS 256
@@ -84,6 +100,14 @@ __device__ __forceinline__ void trace_mark(const SkArgs& A, int t, int slot) {
 }
 
 __device__ __forceinline__ bool sum_ok(float s) { return s > 1e-30f && s < 1e30f; }
+
+// Shared-memory state of the rows a block owns (dynamic shared memory).
+struct RowState {
+    double* phi;    // [2][rows_max]
+    float* fhi;     // [2][rows_max]
+    float* frf;     // [2][rows_max]
+    float* alpha;   // [rows_max]
+};
 
 // ---------------------------------------------------------------------------
 // shared pieces
@@ -112,31 +136,48 @@ __device__ bool prologue_sums(const SkArgs& A, double& inv_sa, double& inv_sb, d
 }
 
 __device__ __forceinline__ void store_col(const SkArgs& A, int buf, int j, double g) {
-    float hi = (float)g;
+    const float hi = (float)g;
     A.gam[buf * A.Ncol + j] = g;
     A.gc[buf * A.Ncol + j] = hi;
     A.cf[buf * A.Ncol + j] = ex2((float)(g - (double)hi));
 }
 
-__device__ __forceinline__ void store_row(const SkArgs& A, int buf, int i, double p) {
-    float hi = (float)p;
+// Row potential for row i (local index li): shared state plus the global copy.
+__device__ __forceinline__ void store_row(const SkArgs& A, const RowState& S, int buf, int i, int li, double p) {
+    const float hi = (float)p;
+    const float rf = ex2((float)(p - (double)hi));
+    S.phi[buf * A.rows_max + li] = p;
+    S.fhi[buf * A.rows_max + li] = hi;
+    S.frf[buf * A.rows_max + li] = rf;
     A.phi[buf * A.M + i] = p;
     A.fhi[buf * A.M + i] = hi;
-    A.frf[buf * A.M + i] = ex2((float)(p - (double)hi));
+    A.frf[buf * A.M + i] = rf;
 }
 
-// Write the returned state (rows and columns from buffer `buf`).
-__device__ void write_outputs(const SkArgs& A, int buf, int r_beg, int r_end, int c_beg, int c_end) {
-    for (int i = r_beg + threadIdx.x; i < r_end; i += OT_BLOCK)
-        A.f_out[i] = A.phi[buf * A.M + i] * A.unit + A.f_shift;
-    for (int j = c_beg + threadIdx.x; j < c_end; j += OT_BLOCK) A.g_out[j] = A.gam[buf * A.Ncol + j] * A.unit;
+// Solver variant codes reported in ot_result.reserved[1].
+#define OT_VARIANT_BULK 1.0
+#define OT_VARIANT_FUSED 2.0
+#define OT_VARIANT_TWOPASS 3.0
+
+__device__ void write_result(const SkArgs& A, int iters, int status, double l1, double variant) {
+    if (threadIdx.x == 0) {
+        A.res->iters = iters;
+        A.res->status = status;
+        A.res->marg_l1 = l1;
+        A.res->marg_l2_col = -1.0;
+        A.res->value = 0.0;
+        A.res->transport_cost = 0.0;
+        A.res->marg_l1_col = -1.0;
+        A.res->reserved[0] = 0.0;
+        A.res->reserved[1] = variant;
+    }
 }
 
-// Sum of the per-block L1 partials, all threads loading in parallel, fixed order.
-__device__ double total_l1(const SkArgs& A, double* s_dred) {
-    double v = 0.0;
-    for (int b2 = threadIdx.x; b2 < gridDim.x; b2 += OT_BLOCK) v += ((volatile double*)A.l1part)[b2];
-    return block_sum_d(v, s_dred);
+__device__ void fail_exit(const SkArgs& A) {
+    if (threadIdx.x == 0) {
+        A.res->iters = -1;
+        A.res->status = ld_volatile_int(&A.ctrl->status);
+    }
 }
 
 // Stopping rule on the state after `done` iterations; returns the status or -1 to continue.
@@ -148,47 +189,14 @@ __device__ __forceinline__ int stop_status(const SkArgs& A, int done, double L1)
     return -1;
 }
 
-__device__ void write_result(const SkArgs& A, int iters, int status, double l1) {
-    if (threadIdx.x == 0) {
-        A.res->iters = iters;
-        A.res->status = status;
-        A.res->marg_l1 = l1;
-        A.res->marg_l2_col = -1.0;
-        A.res->value = 0.0;
-        A.res->transport_cost = 0.0;
-        A.res->marg_l1_col = -1.0;
-    }
-}
-
-__device__ void fail_exit(const SkArgs& A) {
-    if (threadIdx.x == 0) {
-        A.res->iters = -1;
-        A.res->status = ld_volatile_int(&A.ctrl->status);
-    }
-}
-
-// Column update from a finished column sum R (true sum, column factor included):
-// gamma_new = gamma_old - log2(R / beta_j), read from buffer ob, written to nb.
-// Returns false if R is outside the safe range (caller falls back).
-__device__ __forceinline__ bool column_update(const SkArgs& A, int ob, int nb, int j, double R, double inv_sb) {
-    if (R != R) {
-        set_status(A.ctrl, OT_ERR_NONFINITE);
-        return true;
-    }
-    if (!(R > 1e-30 && R < 1e30)) return false;
-    const double beta = (double)A.b[j] * inv_sb;
-    const float d = lg2((float)(R / beta));
-    store_col(A, nb, j, A.gam[ob * A.Ncol + j] - (double)d);
-    return true;
-}
-
-// Robust column update with an explicit max shift over the whole column,
-// from the new row potentials (buffer nb).  Whole block, one column.
+// Robust column update with an explicit max shift over the whole column, from
+// the new row potentials (global buffer nb).  Whole block, one column.
+// Returns the new gamma (thread 0) or NaN after recording OT_ERR_NONFINITE.
 template <bool OTF>
-__device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, float* s_redf) {
-    // row potentials and the new column potential both live in buffer nb
+__device__ double column_fallback(const SkArgs& A, int j, int nb, double inv_sb, float* s_redf) {
     float mx = -INFINITY;
     const float* fh = A.fhi + nb * A.M;
+    const float* fr = A.frf + nb * A.M;
     for (int i = threadIdx.x; i < A.M; i += OT_BLOCK) {
         float c;
         if (OTF) {
@@ -201,6 +209,7 @@ __device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, f
         mx = fmaxf(mx, fmaf(c, -A.kappa, fh[i]));
     }
     mx = warp_max(mx);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) s_redf[threadIdx.x >> 5] = mx;
     __syncthreads();
     float m2 = s_redf[0];
@@ -216,12 +225,12 @@ __device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, f
         } else {
             c = A.C[(long long)i * A.ld + j];
         }
-        s += ex2(fmaf(c, -A.kappa, fh[i]) - m2) * A.frf[nb * A.M + i];
+        s += ex2(fmaf(c, -A.kappa, fh[i]) - m2) * fr[i];
     }
     s = warp_sum(s);
-    __syncthreads();
     if ((threadIdx.x & 31) == 0) s_redf[threadIdx.x >> 5] = s;
     __syncthreads();
+    double gnew = __longlong_as_double(0x7ff8000000000000ll);
     if (threadIdx.x == 0) {
         float tot = 0.f;
         for (int w = 0; w < OT_WARPS; ++w) tot += s_redf[w];
@@ -230,235 +239,743 @@ __device__ void column_fallback(const SkArgs& A, int j, int nb, double inv_sb, f
             set_status(A.ctrl, OT_ERR_NONFINITE);
         } else {
             // gamma_new = log2 beta - (m2 + log2 tot)
-            store_col(A, nb, j, (double)lg2((float)beta) - (double)m2 - (double)lg2(tot));
+            gnew = (double)lg2((float)beta) - (double)m2 - (double)lg2(tot);
+            store_col(A, nb, j, gnew);
         }
     }
     __syncthreads();
+    return gnew;
+}
+
+// Compensated (Kahan) FP32 accumulation.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 // ---------------------------------------------------------------------------
-// Fused single-read kernel (Ncol <= OT_BLOCK * CPT)
+// Fused single-read kernel (stored cost, Ncol <= OT_BLOCK * CPT, Ncol % 4 == 0)
 // ---------------------------------------------------------------------------
 
-// Per-row values the band epilogue needs, loaded at the start of the band so
-// their latency hides behind the band's exponentials.
-struct RowPre {
-    float alpha, fhi, frf;
-    double phi;
-};
-
-template <int CPT, int R, bool SAFE>
-__device__ __forceinline__ void fused_band(const SkArgs& A, int rb, int nr, int cur, int nxt, double inv_sa,
-                                           const float (&gcr)[CPT], const float (&cfr)[CPT], float (&e)[R][CPT],
-                                           double& l1, float (*s_red)[R], float* s_F, float* s_u, int* s_bad) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    RowPre pre = {1.f, 0.f, 1.f, 0.0};
-    if (tid < nr) {
-        const int row = rb + tid;
-        pre.alpha = (float)((double)A.a[row] * inv_sa);
-        if (!SAFE) {
-            pre.fhi = A.fhi[cur * A.M + row];
-            pre.frf = A.frf[cur * A.M + row];
-            pre.phi = A.phi[cur * A.M + row];
+// Sum (or max) of R per-lane values over the 32 lanes of a warp, for all R at
+// once: a transposing butterfly.  At offsets 16, 8, ... each lane keeps half of
+// its values (the upper half if its lane bit is set) and adds the partner's
+// other half; after log2(R) steps one value per lane remains, then plain xor
+// steps finish the reduction.  Lane l ends with the total of value index
+// (l >> (5 - log2 R)) & (R - 1).  R - 1 + (5 - log2 R) shuffles instead of 5R.
+template <int R, bool MAX>
+__device__ __forceinline__ float warp_reduce_rows(float (&v)[R], int lane) {
+    static_assert(R == 4 || R == 8 || R == 16 || R == 32, "R must be a power of two in [4, 32]");
+    constexpr int LOGR = (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : 5;
+#pragma unroll
+    for (int step = 0; step < LOGR; ++step) {
+        const int o = 16 >> step;
+        const int half = R >> (step + 1);
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float keep = up ? v[i + half] : v[i];
+            const float send = up ? v[i] : v[i + half];
+            const float got = __shfl_xor_sync(0xffffffffu, send, o);
+            v[i] = MAX ? fmaxf(keep, got) : keep + got;
         }
     }
-    // 1. exponents x = gamma_j - c_ij (+ phi_i when not SAFE); invalid rows skipped (uniform branch)
+    float x = v[0];
+#pragma unroll
+    for (int o = (16 >> LOGR); o > 0; o >>= 1) {
+        const float got = __shfl_xor_sync(0xffffffffu, x, o);
+        x = MAX ? fmaxf(x, got) : x + got;
+    }
+    return x;
+}
+
+// Band of up to R rows held in shared memory at `sb` (row stride Ncol floats).
+// Thread t owns columns 4*(t + OT_BLOCK*q) + v, v < 4.  Rows r >= nr are
+// computed on -inf exponents (zero entries) so that no per-row branch splits
+// the work.
+//
+// One __syncthreads per band (two in SAFE mode): each warp reduces its R row
+// partial sums with the transposing butterfly and leaves them in s_red (the
+// caller alternates two buffers between bands, so a band's reads never race
+// the next band's writes); after the barrier EVERY warp forms the R row sums
+// lane-parallel (lane r < R sums the OT_WARPS partials of row r) and
+// broadcasts the factors u_r = alpha_r / S_r by shuffles.  Lanes r < nr of
+// warp 0 also record the row's L1 term (into l1, a warp-0 register) and its
+// new potential, off the other warps' critical path.  On return u[] holds the
+// factors; the result says whether some row sum left the safe range (the same
+// answer in every thread of the block).
+template <int CPT, int R, bool SAFE>
+__device__ __forceinline__ bool fused_band(const SkArgs& A, const RowState& RS, const float* sb, int rb, int lb,
+                                           int nr, int cur, int nxt, const float (&gcr)[CPT],
+                                           const float (&cfr)[CPT], float (&e)[R][CPT], float (&u)[R], double& l1,
+                                           float (*s_red)[OT_WARPS]) {
+    static_assert(R <= 32, "one lane per row");
+    constexpr int NV = CPT / 4;
+    constexpr int LOGR = (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int rm = A.rows_max;
+    const int my_row = (lane >> (5 - LOGR)) & (R - 1);          // row reduced into this lane
+    const bool writer = (lane & ((32 >> LOGR) - 1)) == 0;        // one writer lane per row
+    // 1. exponents x = gamma_j - c_ij (+ phi_i when not SAFE)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (r < nr) {
-            const float* crow = A.C + (long long)(rb + r) * A.ld;
-            const float F = SAFE ? 0.f : A.fhi[cur * A.M + rb + r];
+        const bool rv = r < nr;
+        const float4* srow = reinterpret_cast<const float4*>(sb + (size_t)(rv ? r : 0) * A.Ncol);
+        const float F = (SAFE || !rv) ? 0.f : RS.fhi[cur * rm + lb + r];
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                const int j = tid + q * OT_BLOCK;
-                e[r][q] = (j < A.Ncol) ? fmaf(__ldg(crow + j), -A.kappa, gcr[q]) + F : -INFINITY;
+        for (int q = 0; q < NV; ++q) {
+            const int g4 = tid + q * OT_BLOCK;
+            if (rv && 4 * g4 < A.Ncol) {
+                const float4 c = srow[g4];
+                e[r][4 * q + 0] = fmaf(c.x, -A.kappa, gcr[4 * q + 0]) + F;
+                e[r][4 * q + 1] = fmaf(c.y, -A.kappa, gcr[4 * q + 1]) + F;
+                e[r][4 * q + 2] = fmaf(c.z, -A.kappa, gcr[4 * q + 2]) + F;
+                e[r][4 * q + 3] = fmaf(c.w, -A.kappa, gcr[4 * q + 3]) + F;
+            } else {
+                e[r][4 * q + 0] = e[r][4 * q + 1] = e[r][4 * q + 2] = e[r][4 * q + 3] = -INFINITY;
             }
         }
     }
+    float Fsafe = 0.f;   // lane r: -max of row r (SAFE)
     if (SAFE) {
+        float mx[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (r < nr) {
-                float mx = e[r][0];
+            mx[r] = e[r][0];
 #pragma unroll
-                for (int q = 1; q < CPT; ++q) mx = fmaxf(mx, e[r][q]);
-                mx = warp_max(mx);
-                if (lane == 0) s_red[wid][r] = mx;
-            }
+            for (int q = 1; q < CPT; ++q) mx[r] = fmaxf(mx[r], e[r][q]);
         }
+        const float m = warp_reduce_rows<R, true>(mx, lane);
+        if (writer) s_red[my_row][wid] = m;
         __syncthreads();
-        if (tid < nr) {
-            float mx = s_red[0][tid];
-            for (int w = 1; w < OT_WARPS; ++w) mx = fmaxf(mx, s_red[w][tid]);
-            s_F[tid] = (mx > -INFINITY) ? -mx : 0.f;
+        float mm = -INFINITY;
+        if (lane < nr) {
+#pragma unroll
+            for (int w = 0; w < OT_WARPS; ++w) mm = fmaxf(mm, s_red[lane][w]);
         }
-        __syncthreads();
+        Fsafe = (mm > -INFINITY) ? -mm : 0.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (r < nr) {
-                const float F = s_F[r];
+            const float F = __shfl_sync(0xffffffffu, Fsafe, r);
 #pragma unroll
-                for (int q = 0; q < CPT; ++q) e[r][q] += F;
-            }
+            for (int q = 0; q < CPT; ++q) e[r][q] += F;
         }
+        __syncthreads();   // s_red is reused for the sums below
     }
     // 2. e = 2^x * colfactor, row partial sums
+    float ps[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (r < nr) {
-            float s = 0.f;
+        float s = 0.f;
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                e[r][q] = ex2(e[r][q]) * cfr[q];
-                s += e[r][q];
-            }
-            s = warp_sum(s);
-            if (lane == 0) s_red[wid][r] = s;
+        for (int q = 0; q < CPT; ++q) {
+            e[r][q] = ex2(e[r][q]) * cfr[q];
+            s += e[r][q];
+        }
+        ps[r] = s;
+    }
+    const float wsum = warp_reduce_rows<R, false>(ps, lane);
+    if (writer) s_red[my_row][wid] = wsum;
+    __syncthreads();
+    // 3. every warp: lane r forms S_r, u_r; broadcast by shuffles
+    float S = 1.f, alpha = 0.f;
+    if (lane < nr) {
+        const float4* rr = reinterpret_cast<const float4*>(s_red[lane]);
+        const float4 p0 = rr[0], p1 = rr[1];
+        S = ((p0.x + p0.y) + (p0.z + p0.w)) + ((p1.x + p1.y) + (p1.z + p1.w));
+        alpha = RS.alpha[lb + lane];
+    }
+    const bool ok = (lane >= nr) || sum_ok(S);
+    const float ul = (lane < nr) ? __fdividef(alpha, S) : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = __shfl_sync(0xffffffffu, ul, r);
+    const bool bad = !__all_sync(0xffffffffu, ok);
+    if (wid == 0 && lane < nr) {
+        const int li = lb + lane;
+        const float ratio = __fdividef(S, alpha);
+        double pnew;
+        if (!SAFE) {
+            // L1 term of the current state: |S * 2^lo - alpha|
+            l1 += fabs((double)fmaf(S, RS.frf[cur * rm + li] - 1.0f, S - alpha));
+            pnew = (double)RS.fhi[cur * rm + li] - (double)lg2(ratio);
         } else {
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) e[r][q] = 0.f;
+            pnew = (double)Fsafe - (double)lg2(ratio);
         }
+        if (ok) store_row(A, RS, nxt, rb + lane, li, pnew);
     }
-    __syncthreads();
-    // 3. row epilogue: one thread per row
-    if (tid < R) {
-        float u = 0.f;
-        if (tid < nr) {
-            const int row = rb + tid;
-            float S = 0.f;
-#pragma unroll
-            for (int w = 0; w < OT_WARPS; ++w) S += s_red[w][tid];
-            const float alpha = pre.alpha;
-            double pnew;
-            if (!SAFE) {
-                // L1 term of the current state: |S * 2^lo - alpha|
-                l1 += fabs((double)fmaf(S, pre.frf - 1.0f, S - alpha));
-                pnew = (double)pre.fhi - (double)lg2(S / alpha);
-            } else {
-                pnew = (double)s_F[tid] - (double)lg2(S / alpha);
-            }
-            if (sum_ok(S)) {
-                store_row(A, nxt, row, pnew);
-                u = alpha / S;
-            } else {
-                *s_bad = 1;
-            }
-        }
-        s_u[tid] = u;
-    }
-    __syncthreads();
+    return bad;
 }
 
+// Copy band `b` of this block's rows into stage `st` (thread 0 only).
+__device__ __forceinline__ void issue_band(const SkArgs& A, float* smem_bands, unsigned long long* bars, int st,
+                                           int r_beg, int r_end, int R, int b) {
+    const int rb = r_beg + b * R;
+    const int nr = min(R, r_end - rb);
+    const unsigned bytes = (unsigned)nr * (unsigned)A.Ncol * 4u;
+    float* dst = smem_bands + (size_t)st * R * A.Ncol;
+    mbar_arrive_expect_tx(&bars[st], bytes);
+    bulk_g2s(dst, A.C + (long long)rb * A.ld, bytes, &bars[st]);
+}
+
+#define OT_MAX_STAGES 32
+
+// Dynamic shared memory of the fused kernel: [bands][row state][column state].
+__host__ __device__ inline size_t fused_rowstate_bytes(int rows_max) {
+    return (size_t)rows_max * (2 * 8 + 2 * 4 + 2 * 4 + 4);
+}
+__host__ __device__ inline size_t fused_colstate_bytes(int cols_max) { return (size_t)cols_max * (2 * 8 + 4); }
+__host__ __device__ inline size_t align256_hd(size_t x) { return (x + 255) & ~(size_t)255; }
+
 template <int CPT, int R>
-__global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
-    __shared__ float s_red[OT_WARPS][R];
-    __shared__ float s_F[R];
-    __shared__ float s_u[R];
-    __shared__ int s_bad;
+__global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A, int nstage_alloc) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) unsigned long long s_bar[OT_MAX_STAGES];
+    __shared__ __align__(16) float s_red[2][R][OT_WARPS];
     __shared__ double s_dred[OT_WARPS];
     __shared__ float s_redf[OT_WARPS];
-    __shared__ int s_flag_cols[64];
-    __shared__ int s_nflag;
+    __shared__ double s_colred[OT_WARPS][32];
+    __shared__ int s_flag[32];
+    __shared__ int s_copy_ok;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int B = blockIdx.x, G = gridDim.x;
     const int r_beg = (int)((long long)A.M * B / G), r_end = (int)((long long)A.M * (B + 1) / G);
     const int c_beg = (int)((long long)A.Ncol * B / G), c_end = (int)((long long)A.Ncol * (B + 1) / G);
+    const int nbands = (r_end - r_beg + R - 1) / R;
+    const bool resident = A.resident != 0;
+    const int nstage = resident ? nbands : 2;
+
+    float* smem_bands = reinterpret_cast<float*>(dsm);
+    unsigned char* p = dsm + (size_t)nstage_alloc * R * A.Ncol * sizeof(float);
+    RowState RS;
+    RS.phi = reinterpret_cast<double*>(p);
+    RS.fhi = reinterpret_cast<float*>(p + (size_t)A.rows_max * 16);
+    RS.frf = RS.fhi + 2 * A.rows_max;
+    RS.alpha = RS.frf + 2 * A.rows_max;
+    p += align256_hd(fused_rowstate_bytes(A.rows_max));
+    double* s_gam = reinterpret_cast<double*>(p);                      // [2][cols_max]
+    float* s_beta = reinterpret_cast<float*>(p + (size_t)A.cols_max * 16);
+    unsigned epoch = 0;
+
+    // ---- stage the first bands (resident: all of them, once)
+    if (tid == 0) {
+        for (int st = 0; st < nstage; ++st) mbar_init(&s_bar[st], 1);
+        fence_mbar_init();
+        s_copy_ok = 1;
+        if (nbands > 0) {
+            const int first = resident ? nbands : min(2, nbands);
+            for (int u = 0; u < first; ++u) issue_band(A, smem_bands, s_bar, u, r_beg, r_end, R, u % nbands);
+        }
+    }
+    long long issued = nbands > 0 ? (resident ? nbands : min(2, nbands)) : 0;
+    long long consumed = 0;
 
     double inv_sa, inv_sb;
-    if (!prologue_sums(A, inv_sa, inv_sb, s_dred)) {
-        if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0);
-        return;
+    const bool args_ok = prologue_sums(A, inv_sa, inv_sb, s_dred);
+    for (int li = tid; li < r_end - r_beg; li += OT_BLOCK) RS.alpha[li] = (float)((double)A.a[r_beg + li] * inv_sa);
+    for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) {
+        const double g0 = A.warm ? A.g_out[j] / A.unit : 0.0;
+        s_gam[j - c_beg] = g0;
+        s_beta[j - c_beg] = (float)((double)A.b[j] * inv_sb);
+        store_col(A, 0, j, g0);
     }
-    for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) store_col(A, 0, j, A.warm ? A.g_out[j] / A.unit : 0.0);
-    if (tid == 0) { s_bad = 0; s_nflag = 0; }
-    if ((A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
+    bool go = args_ok;
+    if (go && (A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
         withhold_arrival(A.ctrl, A.timeout_ns);
-        fail_exit(A);
-        return;
+        go = false;
+    } else if (go) {
+        go = grid_sync(A.ctrl, G, A.timeout_ns, epoch);
     }
-    if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
 
-    for (int t = 1;; ++t) {
+    for (int t = 1; go; ++t) {
         const int cur = (t - 1) & 1, nxt = cur ^ 1;
         trace_mark(A, t, 0);
         float gcr[CPT], cfr[CPT], acc[CPT];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int j = tid + q * OT_BLOCK;
-            const bool v = j < A.Ncol;
-            gcr[q] = v ? A.gc[cur * A.Ncol + j] : 0.f;
-            cfr[q] = v ? A.cf[cur * A.Ncol + j] : 0.f;
-            acc[q] = 0.f;
+        for (int q = 0; q < CPT / 4; ++q) {
+            const int j4 = tid + q * OT_BLOCK;
+            if (4 * j4 < A.Ncol) {
+                const float4 g4 = reinterpret_cast<const float4*>(A.gc + cur * A.Ncol)[j4];
+                const float4 c4 = reinterpret_cast<const float4*>(A.cf + cur * A.Ncol)[j4];
+                gcr[4 * q] = g4.x; gcr[4 * q + 1] = g4.y; gcr[4 * q + 2] = g4.z; gcr[4 * q + 3] = g4.w;
+                cfr[4 * q] = c4.x; cfr[4 * q + 1] = c4.y; cfr[4 * q + 2] = c4.z; cfr[4 * q + 3] = c4.w;
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) { gcr[4 * q + v] = 0.f; cfr[4 * q + v] = 0.f; }
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[4 * q + v] = 0.f;
         }
         double l1 = 0.0;
         float e[R][CPT];
-        for (int rb = r_beg; rb < r_end; rb += R) {
+        for (int b = 0; b < nbands; ++b) {
+            const int rb = r_beg + b * R;
+            const int lb = b * R;
             const int nr = min(R, r_end - rb);
-            if (t == 1) {
-                fused_band<CPT, R, true>(A, rb, nr, cur, nxt, inv_sa, gcr, cfr, e, l1, s_red, s_F, s_u, &s_bad);
-            } else {
-                fused_band<CPT, R, false>(A, rb, nr, cur, nxt, inv_sa, gcr, cfr, e, l1, s_red, s_F, s_u, &s_bad);
-            }
-            if (s_bad) {   // uniform: read after the band's final __syncthreads
-                __syncthreads();
-                if (tid == 0) s_bad = 0;
-                double dummy = 0.0;
-                fused_band<CPT, R, true>(A, rb, nr, cur, nxt, inv_sa, gcr, cfr, e, dummy, s_red, s_F, s_u, &s_bad);
-                if (s_bad) {
-                    // still out of range after the max shift: non-finite input
-                    if (tid == 0) { set_status(A.ctrl, OT_ERR_NONFINITE); s_bad = 0; }
-                    __syncthreads();
+            const int st = resident ? b : (int)(consumed & 1);
+            // wait for the band's copy (resident: only the first sweep)
+            if (!resident || t == 1) {
+                const unsigned parity = resident ? 0u : (unsigned)((consumed >> 1) & 1);
+                if (tid == 0 && !mbar_wait(&s_bar[st], parity, A.timeout_ns)) {
+                    set_status(A.ctrl, OT_ERR_TIMEOUT);
+                    s_copy_ok = 0;
                 }
+                __syncthreads();
+                if (!s_copy_ok) { go = false; break; }
+            }
+            const float* sb = smem_bands + (size_t)st * R * A.Ncol;
+            float u[R];
+            bool bad;
+            if (t == 1) bad = fused_band<CPT, R, true>(A, RS, sb, rb, lb, nr, cur, nxt, gcr, cfr, e, u, l1, s_red[b & 1]);
+            else bad = fused_band<CPT, R, false>(A, RS, sb, rb, lb, nr, cur, nxt, gcr, cfr, e, u, l1, s_red[b & 1]);
+            if (bad) {   // uniform over the block: redo the band with an explicit max shift
+                __syncthreads();
+                double dummy = 0.0;
+                if (fused_band<CPT, R, true>(A, RS, sb, rb, lb, nr, cur, nxt, gcr, cfr, e, u, dummy, s_red[b & 1]))
+                    if (tid == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
+                __syncthreads();
+            }
+            // every thread has passed the band's barrier, so its shared-memory reads are
+            // done: refill this stage with the band two uses ahead (streaming only)
+            if (!resident) {
+                ++consumed;
+                if (tid == 0) {
+                    fence_proxy_async();
+                    issue_band(A, smem_bands, s_bar, (int)(issued & 1), r_beg, r_end, R, (int)(issued % nbands));
+                }
+                ++issued;
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (r < nr) {
-                    const float u = s_u[r];
 #pragma unroll
-                    for (int q = 0; q < CPT; ++q) acc[q] = fmaf(u, e[r][q], acc[q]);
+                    for (int q = 0; q < CPT; ++q) acc[q] = fmaf(u[r], e[r][q], acc[q]);
                 }
             }
         }
+        if (!go) break;
+        trace_mark(A, t, 4);
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int j = tid + q * OT_BLOCK;
-            if (j < A.Ncol) A.part[(long long)B * A.pstride + j] = acc[q];
+        for (int q = 0; q < CPT / 4; ++q) {
+            const int j4 = tid + q * OT_BLOCK;
+            if (4 * j4 < A.Ncol)
+                reinterpret_cast<float4*>(A.part + (long long)B * A.pstride)[j4] =
+                    make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
         }
-        l1 = block_sum_d(l1, s_dred);
-        if (tid == 0) A.l1part[B] = l1;
+        // only warp 0 holds L1 terms (one lane per row)
+        if (wid == 0) {
+            l1 = warp_sum(l1);
+            if (lane == 0) A.l1part[B] = l1;
+        }
         trace_mark(A, t, 1);
-        if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
         trace_mark(A, t, 2);
 
-        // ---- column phase for owned columns (one warp per column), writes buffer nxt
-        for (int j = c_beg + wid; j < c_end; j += OT_WARPS) {
-            double s = 0.0;
-            for (int b2 = lane; b2 < G; b2 += 32) s += (double)A.part[(long long)b2 * A.pstride + j];
-            s = warp_sum(s);
-            if (lane == 0) {
-                if (!column_update(A, cur, nxt, j, s, inv_sb)) {
-                    const int k = atomicAdd(&s_nflag, 1);
-                    if (k < 64) s_flag_cols[k] = j;
-                    else set_status(A.ctrl, OT_ERR_NONFINITE);
+        // ---- column phase: lane <-> owned column, warps split the block partials
+        double l1v = 0.0;
+        for (int b2 = tid; b2 < G; b2 += OT_BLOCK) l1v += ((volatile double*)A.l1part)[b2];
+        for (int c0 = c_beg; c0 < c_end; c0 += 32) {
+            const int j = c0 + lane;
+            const bool jv = j < c_end;
+            float s = 0.f, comp = 0.f;
+            for (int base = 0; base < G; base += OT_WARPS * 20) {
+                float v[20];   // all loads in flight before the compensated sum
+#pragma unroll
+                for (int k = 0; k < 20; ++k) {
+                    const int b2 = base + wid + k * OT_WARPS;
+                    v[k] = (jv && b2 < G) ? A.part[(long long)b2 * A.pstride + j] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 20; ++k) kahan_add(s, comp, v[k]);
+            }
+            s_colred[wid][lane] = (double)s - (double)comp;
+            __syncthreads();
+            if (wid == 0) {
+                int bad = 0;
+                if (jv) {
+                    double R2 = 0.0;
+#pragma unroll
+                    for (int w = 0; w < OT_WARPS; ++w) R2 += s_colred[w][lane];
+                    const int cl = j - c_beg;
+                    if (R2 != R2) {
+                        set_status(A.ctrl, OT_ERR_NONFINITE);
+                    } else if (R2 > 1e-30 && R2 < 1e30) {
+                        const double gnew = s_gam[cur * A.cols_max + cl] - (double)lg2(__fdividef((float)R2, s_beta[cl]));
+                        s_gam[nxt * A.cols_max + cl] = gnew;
+                        store_col(A, nxt, j, gnew);
+                    } else {
+                        bad = 1;
+                    }
+                }
+                s_flag[lane] = bad;
+            }
+            __syncthreads();
+            for (int l = 0; l < 32; ++l) {
+                if (s_flag[l]) {   // rare: a column sum out of range, redo with an explicit max
+                    const double gnew = column_fallback<false>(A, c0 + l, nxt, inv_sb, s_redf);
+                    if (tid == 0) s_gam[nxt * A.cols_max + (c0 + l - c_beg)] = gnew;
                 }
             }
         }
-        // ---- stopping rule on the state after iteration t-1 (overlaps the column phase)
-        const double L1 = total_l1(A, s_dred);
-        const int st = stop_status(A, t - 1, L1);
-        if (st >= 0) {
-            write_outputs(A, cur, r_beg, r_end, c_beg, c_end);
-            if (B == 0) write_result(A, t - 1, st, L1);
-            return;
+        trace_mark(A, t, 6);
+        // ---- stopping rule on the state after iteration t-1 (its L1 was loaded above)
+        const double L1 = block_sum_d(l1v, s_dred);
+        trace_mark(A, t, 7);
+        const int stt = stop_status(A, t - 1, L1);
+        if (stt >= 0) {
+            for (int li = tid; li < r_end - r_beg; li += OT_BLOCK)
+                A.f_out[r_beg + li] = RS.phi[cur * A.rows_max + li] * A.unit + A.f_shift;
+            for (int j = c_beg + tid; j < c_end; j += OT_BLOCK)
+                A.g_out[j] = s_gam[cur * A.cols_max + (j - c_beg)] * A.unit;
+            if (B == 0) write_result(A, t - 1, stt, L1, OT_VARIANT_FUSED);
+            break;
         }
-        const int nflag = min(s_nflag, 64);
-        __syncthreads();
-        if (tid == 0) s_nflag = 0;
-        for (int k = 0; k < nflag; ++k) column_fallback<false>(A, s_flag_cols[k], nxt, inv_sb, s_redf);
         trace_mark(A, t, 3);
-        if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
     }
+    if (!args_ok) {
+        if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0, OT_VARIANT_FUSED);
+    } else if (!go) {
+        fail_exit(A);
+    }
+    // drain copies still in flight into this block's shared memory before leaving
+    if (tid == 0 && nbands > 0) {
+        if (!resident) {
+            for (long long u = consumed; u < issued; ++u)
+                if (!mbar_wait(&s_bar[u & 1], (unsigned)((u >> 1) & 1), A.timeout_ns)) break;
+        } else {
+            for (int st = 0; st < nstage; ++st) mbar_wait(&s_bar[st], 0u, A.timeout_ns);
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-reduce kernel: the fused sweep with ONE grid barrier per sweep
+// ---------------------------------------------------------------------------
+//
+// After its row phase every block adds its column partials (FP64, plus its L1
+// term in slot Ncol) into one global vector with a single bulk asynchronous
+// reduce-add (cp.reduce.async.bulk ... .add.f64: the TMA unit performs the
+// adds at L2).  One grid barrier; then EVERY block reads the finished vector
+// and updates the potentials of the columns it holds in registers (identical
+// arithmetic in every block, hence identical results).  Column potentials
+// never travel through global memory and there is no second barrier.  The
+// vector is triple-buffered: written in sweep t, read after barrier t, zeroed
+// (in slices, by all blocks) between barriers t+1 and t+2, written again in
+// sweep t+3.  Each buffer may hold OT_ACC_COPIES copies (block b adds into copy
+// b mod OT_ACC_COPIES, readers sum the copies); measured on GB300, one copy is
+// fastest overall: spreading the L2 adds over copies shortens the barrier wait
+// but costs as much again in reads.  Column potentials are FP32 hi/lo pairs
+// (double-float).  FP64
+// adds in a run-dependent order make the last bits of a column sum vary from
+// run to run; every block still sees the same value.
+
+// (hi, lo) -= d, renormalised (two-sum, then fast two-sum).
+__device__ __forceinline__ void df_sub(float& hi, float& lo, float d) {
+    const float s = hi - d;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (-d - bb);
+    const float t = err + lo;
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
+#define OT_ACC_COPIES 1
+
+__device__ __forceinline__ void bulk_reduce_add_f64(double* gdst, const double* ssrc, unsigned bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_addr(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <int CPT, int R>
+__global__ void __launch_bounds__(OT_BLOCK, 1) sk_bulk_kernel(SkArgs A, int nstage_alloc) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) unsigned long long s_bar[OT_MAX_STAGES];
+    __shared__ __align__(16) float s_red[2][R][OT_WARPS];
+    __shared__ double s_dred[OT_WARPS];
+    __shared__ float s_redf[OT_WARPS];
+    __shared__ int s_copy_ok;
+    __shared__ int s_nfix;
+    __shared__ int s_fix[64];
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int B = blockIdx.x, G = gridDim.x;
+    const int Nc = A.Ncol;
+    const int vlen = Nc + 2;                     // column sums, L1, pad
+    const int r_beg = (int)((long long)A.M * B / G), r_end = (int)((long long)A.M * (B + 1) / G);
+    const int o_beg = (int)((long long)Nc * B / G), o_end = (int)((long long)Nc * (B + 1) / G);
+    const long long zlen = (long long)OT_ACC_COPIES * A.vstride;   // one buffer, all copies
+    const int z_beg = (int)(zlen * B / G), z_end = (int)(zlen * (B + 1) / G);
+    const int nbands = (r_end - r_beg + R - 1) / R;
+    const bool resident = A.resident != 0;
+    const int nstage = resident ? nbands : 2;
+
+    float* smem_bands = reinterpret_cast<float*>(dsm);
+    unsigned char* p = dsm + (size_t)nstage_alloc * R * Nc * sizeof(float);
+    double* s_part = reinterpret_cast<double*>(p);                     // [vlen]
+    p += align256_hd((size_t)vlen * sizeof(double));
+    float* s_glo = reinterpret_cast<float*>(p);                        // [Ncol] gamma lo
+    float* s_ghi = s_glo + Nc;                                         // [Ncol] gamma hi
+    float* s_beta = s_ghi + Nc;                                        // [Ncol]
+    p += align256_hd((size_t)3 * Nc * sizeof(float));
+    RowState RS;
+    RS.phi = reinterpret_cast<double*>(p);
+    RS.fhi = reinterpret_cast<float*>(p + (size_t)A.rows_max * 16);
+    RS.frf = RS.fhi + 2 * A.rows_max;
+    RS.alpha = RS.frf + 2 * A.rows_max;
+    double* acc_g = A.acc;                                              // [3][vstride]
+    unsigned epoch = 0;
+
+    if (tid == 0) {
+        for (int st = 0; st < nstage; ++st) mbar_init(&s_bar[st], 1);
+        fence_mbar_init();
+        s_copy_ok = 1;
+        s_nfix = 0;
+        if (nbands > 0) {
+            const int first = resident ? nbands : min(2, nbands);
+            for (int u = 0; u < first; ++u) issue_band(A, smem_bands, s_bar, u, r_beg, r_end, R, u % nbands);
+        }
+    }
+    long long issued = nbands > 0 ? (resident ? nbands : min(2, nbands)) : 0;
+    long long consumed = 0;
+
+    double inv_sa, inv_sb;
+    const bool args_ok = prologue_sums(A, inv_sa, inv_sb, s_dred);
+    for (int li = tid; li < r_end - r_beg; li += OT_BLOCK) RS.alpha[li] = (float)((double)A.a[r_beg + li] * inv_sa);
+    for (int j = tid; j < Nc; j += OT_BLOCK) s_beta[j] = (float)((double)A.b[j] * inv_sb);
+    float gcr[CPT], cfr[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT / 4; ++q) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = 4 * (tid + q * OT_BLOCK) + v;
+            float hi = 0.f, lo = 0.f;
+            if (j < Nc) {
+                const double g0 = A.warm ? A.g_out[j] / A.unit : 0.0;
+                split_f64(g0, hi, lo);
+                s_ghi[j] = hi;
+                s_glo[j] = lo;
+            }
+            gcr[4 * q + v] = hi;
+            cfr[4 * q + v] = (j < Nc) ? ex2(lo) : 0.f;
+        }
+    }
+    bool go = args_ok;
+    if (go && (A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
+        withhold_arrival(A.ctrl, A.timeout_ns);
+        go = false;
+    } else if (go) {
+        go = grid_sync(A.ctrl, G, A.timeout_ns, epoch);
+    }
+
+    for (int t = 1; go; ++t) {
+        const int cur = (t - 1) & 1, nxt = cur ^ 1;
+        const size_t bufsz = (size_t)OT_ACC_COPIES * A.vstride;
+        double* vec = acc_g + (size_t)(t % 3) * bufsz;                  // this sweep's sums (all copies)
+        double* vmine = vec + (size_t)(B % OT_ACC_COPIES) * A.vstride;  // the copy this block adds into
+        double* vzero = acc_g + (size_t)((t + 2) % 3) * bufsz;          // read in sweep t-1: clear it
+        trace_mark(A, t, 0);
+        float acc[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
+        double l1 = 0.0;
+        float e[R][CPT];
+        for (int b = 0; b < nbands; ++b) {
+            const int rb = r_beg + b * R;
+            const int lb = b * R;
+            const int nr = min(R, r_end - rb);
+            const int st = resident ? b : (int)(consumed & 1);
+            if (!resident || t == 1) {
+                const unsigned parity = resident ? 0u : (unsigned)((consumed >> 1) & 1);
+                if (tid == 0 && !mbar_wait(&s_bar[st], parity, A.timeout_ns)) {
+                    set_status(A.ctrl, OT_ERR_TIMEOUT);
+                    s_copy_ok = 0;
+                }
+                __syncthreads();
+                if (!s_copy_ok) { go = false; break; }
+            }
+            const float* sb = smem_bands + (size_t)st * R * Nc;
+            float u[R];
+            bool bad;
+            if (t == 1) bad = fused_band<CPT, R, true>(A, RS, sb, rb, lb, nr, cur, nxt, gcr, cfr, e, u, l1, s_red[b & 1]);
+            else bad = fused_band<CPT, R, false>(A, RS, sb, rb, lb, nr, cur, nxt, gcr, cfr, e, u, l1, s_red[b & 1]);
+            if (bad) {   // uniform over the block: redo the band with an explicit max shift
+                __syncthreads();
+                double dummy = 0.0;
+                if (fused_band<CPT, R, true>(A, RS, sb, rb, lb, nr, cur, nxt, gcr, cfr, e, u, dummy, s_red[b & 1]))
+                    if (tid == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
+                __syncthreads();
+            }
+            if (!resident) {
+                ++consumed;
+                if (tid == 0) {
+                    fence_proxy_async();
+                    issue_band(A, smem_bands, s_bar, (int)(issued & 1), r_beg, r_end, R, (int)(issued % nbands));
+                }
+                ++issued;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < nr) {
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) acc[q] = fmaf(u[r], e[r][q], acc[q]);
+                }
+            }
+        }
+        if (!go) break;
+        trace_mark(A, t, 4);
+        // ---- block partials (FP64) + L1 into shared memory, one bulk reduce-add into the global vector
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+            const int j4 = tid + q * OT_BLOCK;
+            if (4 * j4 < Nc) {
+                double2* dst = reinterpret_cast<double2*>(s_part + 4 * j4);
+                dst[0] = make_double2((double)acc[4 * q], (double)acc[4 * q + 1]);
+                dst[1] = make_double2((double)acc[4 * q + 2], (double)acc[4 * q + 3]);
+            }
+        }
+        if (wid == 0) {   // only warp 0 holds L1 terms (one lane per row)
+            l1 = warp_sum(l1);
+            if (lane == 0) { s_part[Nc] = l1; s_part[Nc + 1] = 0.0; }
+        }
+        fence_proxy_async();   // this thread's shared-memory writes -> visible to the bulk copy
+        __syncthreads();
+        if (tid == 0) {
+            fence_proxy_async_global();   // the slice clears of earlier sweeps precede this reduce
+            // two pieces starting at a block-dependent offset (a multiple of 2 doubles), so the
+            // blocks' adds do not all hit the same L2 sectors at the same time
+            const int rot = (int)(((long long)(vlen / 2) * B / G) * 2);
+            if (rot > 0) bulk_reduce_add_f64(vmine, s_part, (unsigned)(rot * sizeof(double)));
+            bulk_reduce_add_f64(vmine + rot, s_part + rot, (unsigned)((vlen - rot) * sizeof(double)));
+            bulk_wait_all();
+            fence_proxy_async_global();
+        }
+        trace_mark(A, t, 1);
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
+        trace_mark(A, t, 2);
+
+        // ---- column sums of this thread's columns and the L1 of the state, all loads issued
+        // before any use: every copy's entries unconditionally (clamped index), L1 lane-parallel
+        double2 r01[CPT / 4][OT_ACC_COPIES], r23[CPT / 4][OT_ACC_COPIES];
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+            const int j4 = min(tid + q * OT_BLOCK, Nc / 4 - 1);
+#pragma unroll
+            for (int c = 0; c < OT_ACC_COPIES; ++c) {
+                const double2* src = reinterpret_cast<const double2*>(vec + (size_t)c * A.vstride + 4 * j4);
+                r01[q][c] = __ldcg(src);
+                r23[q][c] = __ldcg(src + 1);
+            }
+        }
+        double L1 = (lane < OT_ACC_COPIES) ? __ldcg(vec + (size_t)lane * A.vstride + Nc) : 0.0;
+        L1 = warp_sum(L1);
+        double Rcol[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+            // pairwise sums of the copies (fixed order)
+#pragma unroll
+            for (int w = OT_ACC_COPIES / 2; w > 0; w /= 2)
+#pragma unroll
+                for (int c = 0; c < w; ++c) {
+                    r01[q][c].x += r01[q][c + w].x; r01[q][c].y += r01[q][c + w].y;
+                    r23[q][c].x += r23[q][c + w].x; r23[q][c].y += r23[q][c + w].y;
+                }
+            Rcol[4 * q] = r01[q][0].x; Rcol[4 * q + 1] = r01[q][0].y;
+            Rcol[4 * q + 2] = r23[q][0].x; Rcol[4 * q + 3] = r23[q][0].y;
+        }
+        trace_mark(A, t, 5);
+        const int stt = stop_status(A, t - 1, L1);
+        if (stt >= 0) {
+            for (int li = tid; li < r_end - r_beg; li += OT_BLOCK)
+                A.f_out[r_beg + li] = RS.phi[cur * A.rows_max + li] * A.unit + A.f_shift;
+            for (int j = o_beg + tid; j < o_end; j += OT_BLOCK)
+                A.g_out[j] = ((double)s_ghi[j] + (double)s_glo[j]) * A.unit;
+            if (B == 0) write_result(A, t - 1, stt, L1, OT_VARIANT_BULK);
+            break;
+        }
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+            const int j4 = tid + q * OT_BLOCK;
+            if (4 * j4 < Nc) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int j = 4 * j4 + v;
+                    const double Rj = Rcol[4 * q + v];
+                    if (Rj != Rj) {
+                        set_status(A.ctrl, OT_ERR_NONFINITE);
+                    } else if (Rj > 1e-30 && Rj < 1e30) {
+                        float hi = gcr[4 * q + v], lo = s_glo[j];
+                        df_sub(hi, lo, lg2(__fdividef((float)Rj, s_beta[j])));
+                        gcr[4 * q + v] = hi;
+                        cfr[4 * q + v] = ex2(lo);
+                        s_ghi[j] = hi;
+                        s_glo[j] = lo;
+                    } else {
+                        const int k2 = atomicAdd(&s_nfix, 1);
+                        if (k2 < 64) s_fix[k2] = j;
+                        else set_status(A.ctrl, OT_ERR_NONFINITE);
+                    }
+                }
+            }
+        }
+        trace_mark(A, t, 6);
+        // clear this block's slice of the vector read in sweep t-1 (next written in sweep t+2)
+        if (z_beg + tid < z_end) {
+            for (int k = z_beg + tid; k < z_end; k += OT_BLOCK) vzero[k] = 0.0;   // slice of all copies
+            fence_proxy_async_global();   // by the writing threads: clears ordered before later bulk adds
+        }
+        __syncthreads();
+        trace_mark(A, t, 7);
+        const int nfix = min(s_nfix, 64);
+        if (nfix > 0) {   // rare: column sums out of range, recomputed with an explicit max by every block
+            for (int k = 0; k < nfix; ++k) {
+                const int j = s_fix[k];
+                const double gnew = column_fallback<false>(A, j, nxt, inv_sb, s_redf);
+                if (tid == 0) {
+                    float hi, lo;
+                    split_f64(gnew, hi, lo);
+                    s_ghi[j] = hi;
+                    s_glo[j] = lo;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) s_nfix = 0;
+#pragma unroll
+            for (int q = 0; q < CPT / 4; ++q)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int j = 4 * (tid + q * OT_BLOCK) + v;
+                    if (j < Nc) { gcr[4 * q + v] = s_ghi[j]; cfr[4 * q + v] = ex2(s_glo[j]); }
+                }
+            __syncthreads();
+        }
+        trace_mark(A, t, 3);
+    }
+    if (!args_ok) {
+        if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0, OT_VARIANT_BULK);
+    } else if (!go) {
+        fail_exit(A);
+    }
+    if (tid == 0 && nbands > 0) {
+        if (!resident) {
+            for (long long u = consumed; u < issued; ++u)
+                if (!mbar_wait(&s_bar[u & 1], (unsigned)((u >> 1) & 1), A.timeout_ns)) break;
+        } else {
+            for (int st = 0; st < nstage; ++st) mbar_wait(&s_bar[st], 0u, A.timeout_ns);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -470,20 +987,12 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A) {
 // Row phase for a band of up to WR rows: S_r = sum_j 2^(F_r + gamma_j - c_rj) * cf_j.
 // SAFE: F_r = -max_j(gamma_j - c_rj) (extra pass).  Writes phi_new; adds L1.
 template <bool OTF, bool SAFE>
-__device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int nxt, double inv_sa, double& l1,
-                                 float (*s_red)[WR], float* s_F, int* s_bad) {
+__device__ void twopass_row_band(const SkArgs& A, const RowState& RS, int rb, int lb, int nr, int cur, int nxt,
+                                 double& l1, float (*s_red)[WR], float* s_F, int* s_bad) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int rm = A.rows_max;
     const float* gcp = A.gc + cur * A.Ncol;
     const float* cfp = A.cf + cur * A.Ncol;
-    RowPre pre = {1.f, 0.f, 1.f, 0.0};
-    if (tid < nr) {
-        const int row = rb + tid;
-        pre.alpha = (float)((double)A.a[row] * inv_sa);
-        if (!SAFE) {
-            pre.fhi = A.fhi[cur * A.M + row];
-            pre.frf = A.frf[cur * A.M + row];
-        }
-    }
     float F[WR];
     float2 xr[WR];
     const float* crow[WR];
@@ -492,7 +1001,7 @@ __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int n
         const int row = rb + (r < nr ? r : 0);
         xr[r] = OTF ? __ldg(A.X + row) : make_float2(0.f, 0.f);
         crow[r] = OTF ? nullptr : A.C + (long long)row * A.ld;
-        F[r] = (!SAFE && r < nr) ? A.fhi[cur * A.M + row] : 0.f;
+        F[r] = (!SAFE && r < nr) ? RS.fhi[cur * rm + lb + r] : 0.f;
     }
     if (SAFE) {
         float mx[WR];
@@ -559,18 +1068,18 @@ __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int n
     }
     __syncthreads();
     if (tid < nr) {
-        const int row = rb + tid;
+        const int li = lb + tid;
         float S = 0.f;
         for (int w = 0; w < OT_WARPS; ++w) S += s_red[w][tid];
-        const float alpha = pre.alpha;
+        const float alpha = RS.alpha[li];
         double pnew;
         if (!SAFE) {
-            l1 += fabs((double)fmaf(S, pre.frf - 1.0f, S - alpha));
-            pnew = (double)pre.fhi - (double)lg2(S / alpha);
+            l1 += fabs((double)fmaf(S, RS.frf[cur * rm + li] - 1.0f, S - alpha));
+            pnew = (double)RS.fhi[cur * rm + li] - (double)lg2(S / alpha);
         } else {
             pnew = (double)s_F[tid] - (double)lg2(S / alpha);
         }
-        if (sum_ok(S)) store_row(A, nxt, row, pnew);
+        if (sum_ok(S)) store_row(A, RS, nxt, rb + tid, li, pnew);
         else *s_bad = 1;
     }
     __syncthreads();
@@ -578,6 +1087,7 @@ __device__ void twopass_row_band(const SkArgs& A, int rb, int nr, int cur, int n
 
 template <bool OTF>
 __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
+    extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ float s_red[OT_WARPS][WR];
     __shared__ float s_F[WR];
     __shared__ int s_bad;
@@ -585,68 +1095,91 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
     __shared__ float s_redf[OT_WARPS];
     __shared__ float s_col[OT_WARPS][32];
     __shared__ int s_flag[32];
+    __shared__ unsigned s_chunk;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int B = blockIdx.x, G = gridDim.x;
     const int r_beg = (int)((long long)A.M * B / G), r_end = (int)((long long)A.M * (B + 1) / G);
-    // columns are handed out in chunks of 32 (one lane per column)
+    // static column ranges (initialisation and output), in chunks of 32
     const int nchunks = (A.Ncol + 31) / 32;
     const int k_beg = (int)((long long)nchunks * B / G), k_end = (int)((long long)nchunks * (B + 1) / G);
     const int c_beg = min(A.Ncol, k_beg * 32), c_end = min(A.Ncol, k_end * 32);
+    RowState RS;
+    RS.phi = reinterpret_cast<double*>(dsm);
+    RS.fhi = reinterpret_cast<float*>(dsm + (size_t)A.rows_max * 16);
+    RS.frf = RS.fhi + 2 * A.rows_max;
+    RS.alpha = RS.frf + 2 * A.rows_max;
+    unsigned epoch = 0;
 
     double inv_sa, inv_sb;
-    if (!prologue_sums(A, inv_sa, inv_sb, s_dred)) {
-        if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0);
-        return;
-    }
+    const bool args_ok = prologue_sums(A, inv_sa, inv_sb, s_dred);
+    for (int li = tid; li < r_end - r_beg; li += OT_BLOCK) RS.alpha[li] = (float)((double)A.a[r_beg + li] * inv_sa);
     for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) store_col(A, 0, j, A.warm ? A.g_out[j] / A.unit : 0.0);
+    if (B == 0 && tid == 0) { A.queue[0] = 0; A.queue[1] = 0; }
     if (tid == 0) s_bad = 0;
-    if ((A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
+    bool go = args_ok;
+    if (go && (A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
         withhold_arrival(A.ctrl, A.timeout_ns);
-        fail_exit(A);
-        return;
+        go = false;
+    } else if (go) {
+        go = grid_sync(A.ctrl, G, A.timeout_ns, epoch);
     }
-    if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
 
-    for (int t = 1;; ++t) {
+    for (int t = 1; go; ++t) {
         const int cur = (t - 1) & 1, nxt = cur ^ 1;
         trace_mark(A, t, 0);
         double l1 = 0.0;
         for (int rb = r_beg; rb < r_end; rb += WR) {
             const int nr = min(WR, r_end - rb);
-            if (t == 1) twopass_row_band<OTF, true>(A, rb, nr, cur, nxt, inv_sa, l1, s_red, s_F, &s_bad);
-            else twopass_row_band<OTF, false>(A, rb, nr, cur, nxt, inv_sa, l1, s_red, s_F, &s_bad);
+            const int lb = rb - r_beg;
+            if (t == 1) twopass_row_band<OTF, true>(A, RS, rb, lb, nr, cur, nxt, l1, s_red, s_F, &s_bad);
+            else twopass_row_band<OTF, false>(A, RS, rb, lb, nr, cur, nxt, l1, s_red, s_F, &s_bad);
             if (s_bad) {
                 __syncthreads();
                 if (tid == 0) s_bad = 0;
                 double dummy = 0.0;
-                twopass_row_band<OTF, true>(A, rb, nr, cur, nxt, inv_sa, dummy, s_red, s_F, &s_bad);
+                twopass_row_band<OTF, true>(A, RS, rb, lb, nr, cur, nxt, dummy, s_red, s_F, &s_bad);
                 if (s_bad) {
                     if (tid == 0) { set_status(A.ctrl, OT_ERR_NONFINITE); s_bad = 0; }
                     __syncthreads();
                 }
             }
         }
-        l1 = block_sum_d(l1, s_dred);
-        if (tid == 0) A.l1part[B] = l1;
+        // only warp 0 holds L1 terms (one lane per row)
+        if (wid == 0) {
+            l1 = warp_sum(l1);
+            if (lane == 0) A.l1part[B] = l1;
+        }
         trace_mark(A, t, 1);
-        if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
         trace_mark(A, t, 2);
 
-        const double L1 = total_l1(A, s_dred);
-        const int st = stop_status(A, t - 1, L1);
-        if (st >= 0) {
-            write_outputs(A, cur, r_beg, r_end, c_beg, c_end);
-            if (B == 0) write_result(A, t - 1, st, L1);
-            return;
+        double l1v = 0.0;
+        for (int b2 = tid; b2 < G; b2 += OT_BLOCK) l1v += ((volatile double*)A.l1part)[b2];
+        const double L1 = block_sum_d(l1v, s_dred);
+        const int stt = stop_status(A, t - 1, L1);
+        if (stt >= 0) {
+            for (int li = tid; li < r_end - r_beg; li += OT_BLOCK)
+                A.f_out[r_beg + li] = RS.phi[cur * A.rows_max + li] * A.unit + A.f_shift;
+            for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) A.g_out[j] = A.gam[cur * A.Ncol + j] * A.unit;
+            if (B == 0) write_result(A, t - 1, stt, L1, OT_VARIANT_TWOPASS);
+            break;
         }
+        // the queue of the next sweep is idle now (every block has left the previous column pass)
+        if (B == 0 && tid == 0) A.queue[nxt] = 0;
 
-        // ---- column pass: lane <-> column, warps split the rows; writes buffer nxt
+        // ---- column pass over dynamically claimed 32-column chunks: lane <-> column, warps split rows
         const float* fh = A.fhi + nxt * A.M;
         const float* fr = A.frf + nxt * A.M;
-        for (int c0 = c_beg; c0 < c_end; c0 += 32) {
+        for (;;) {
+            if (tid == 0) s_chunk = atomicAdd(&A.queue[cur], 1u);
+            __syncthreads();
+            const int chunk = (int)s_chunk;
+            __syncthreads();
+            if (chunk >= nchunks) break;
+            const int c0 = chunk * 32;
             const int j = c0 + lane;
-            const bool jv = j < c_end;
+            const bool jv = j < A.Ncol;
             const float g = jv ? A.gc[cur * A.Ncol + j] : 0.f;
             const float2 yj = (OTF && jv) ? __ldg(A.Y + j) : make_float2(0.f, 0.f);
             float s = 0.f;
@@ -668,10 +1201,17 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
             if (wid == 0) {
                 int bad = 0;
                 if (jv) {
-                    double R = 0.0;
-                    for (int w = 0; w < OT_WARPS; ++w) R += (double)s_col[w][lane];
-                    R *= (double)A.cf[cur * A.Ncol + j];
-                    bad = !column_update(A, cur, nxt, j, R, inv_sb);
+                    double R2 = 0.0;
+                    for (int w = 0; w < OT_WARPS; ++w) R2 += (double)s_col[w][lane];
+                    R2 *= (double)A.cf[cur * A.Ncol + j];
+                    if (R2 != R2) {
+                        set_status(A.ctrl, OT_ERR_NONFINITE);
+                    } else if (R2 > 1e-30 && R2 < 1e30) {
+                        const double beta = (double)A.b[j] * inv_sb;
+                        store_col(A, nxt, j, A.gam[cur * A.Ncol + j] - (double)lg2((float)(R2 / beta)));
+                    } else {
+                        bad = 1;
+                    }
                 }
                 s_flag[lane] = bad;
             }
@@ -680,7 +1220,12 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
                 if (s_flag[l]) column_fallback<OTF>(A, c0 + l, nxt, inv_sb, s_redf);
         }
         trace_mark(A, t, 3);
-        if (!grid_sync(A.ctrl, G, A.timeout_ns)) { fail_exit(A); return; }
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
+    }
+    if (!args_ok) {
+        if (B == 0) write_result(A, 0, OT_ERR_ARG, -1.0, OT_VARIANT_TWOPASS);
+    } else if (!go) {
+        fail_exit(A);
     }
 }
 
@@ -688,10 +1233,9 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
 // host side
 // ---------------------------------------------------------------------------
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 struct WsLayout {
-    size_t ctrl, phi, fhi, frf, gam, gc, cf, part, l1part, trace, total;
+    size_t ctrl, phi, fhi, frf, gam, gc, cf, part, l1part, queue, acc, trace, total;
+    int vstride;
     int pstride;
 };
 
@@ -699,21 +1243,26 @@ static WsLayout ws_layout(int M, int Ncol, int grid, bool fused) {
     WsLayout L;
     L.pstride = (Ncol + 3) & ~3;
     size_t o = 0;
-    L.ctrl = o; o = align256(o + sizeof(Ctrl));
-    L.phi = o; o = align256(o + sizeof(double) * 2 * (size_t)M);
-    L.fhi = o; o = align256(o + sizeof(float) * 2 * (size_t)M);
-    L.frf = o; o = align256(o + sizeof(float) * 2 * (size_t)M);
-    L.gam = o; o = align256(o + sizeof(double) * 2 * (size_t)Ncol);
-    L.gc = o; o = align256(o + sizeof(float) * 2 * (size_t)Ncol);
-    L.cf = o; o = align256(o + sizeof(float) * 2 * (size_t)Ncol);
-    L.part = o; o = align256(o + (fused ? sizeof(float) * (size_t)grid * L.pstride : 0));
-    L.l1part = o; o = align256(o + sizeof(double) * (size_t)grid);
-    L.trace = o; o = align256(o + sizeof(unsigned long long) * 8 * OT_TRACE_SWEEPS);
+    L.ctrl = o; o = align256_hd(o + sizeof(Ctrl));
+    L.phi = o; o = align256_hd(o + sizeof(double) * 2 * (size_t)M);
+    L.fhi = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)M);
+    L.frf = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)M);
+    L.gam = o; o = align256_hd(o + sizeof(double) * 2 * (size_t)Ncol);
+    L.gc = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)Ncol);
+    L.cf = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)Ncol);
+    L.part = o; o = align256_hd(o + (fused ? sizeof(float) * (size_t)grid * L.pstride : 0));
+    L.l1part = o; o = align256_hd(o + sizeof(double) * (size_t)grid);
+    L.queue = o; o = align256_hd(o + sizeof(unsigned) * 2);
+    L.vstride = ((Ncol + 2) + 31) & ~31;
+    L.acc = o; o = align256_hd(o + (fused ? sizeof(double) * 3 * OT_ACC_COPIES * (size_t)L.vstride : 0));
+    L.trace = o; o = align256_hd(o + sizeof(unsigned long long) * 8 * OT_TRACE_SWEEPS);
     L.total = o;
     return L;
 }
 
 static const int kFusedMaxCols = OT_BLOCK * 16;
+static const int kFusedMaxRowsPerBlock = 128;
+static const size_t kSmemBudget = 200 * 1024;
 
 static int solver_grid(int M) {
     int sms = device_sms();
@@ -724,38 +1273,84 @@ static int solver_grid(int M) {
     return g;
 }
 
+static bool fused_ok(const SkArgs& A, int grid) {
+    return A.C != nullptr && A.Ncol <= kFusedMaxCols && A.Ncol % 4 == 0 && A.ld == A.Ncol &&
+           ((uintptr_t)A.C) % 16 == 0 && (A.M + grid - 1) / grid <= kFusedMaxRowsPerBlock &&
+           (A.Ncol + grid - 1) / grid <= kFusedMaxRowsPerBlock;
+}
+
 size_t solver_ws_bytes(int M, int Ncol, bool stored) {
-    const bool fused = stored && Ncol <= kFusedMaxCols;
+    const bool fused = stored && Ncol <= kFusedMaxCols;   // partial buffer sized whenever it may be used
     const int grid = solver_grid(M);
     if (grid <= 0) return 0;
     return ws_layout(M, Ncol, grid, fused).total;
 }
 
-template <typename K>
-static int coop_launch(K kernel, int grid, SkArgs& A, cudaStream_t st) {
+template <typename K, typename... Args>
+static int coop_launch(K kernel, int grid, cudaStream_t st, size_t smem, Args... args) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return OT_ERR_CUDA;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, OT_BLOCK, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, OT_BLOCK, smem) != cudaSuccess || nb < 1)
         return OT_ERR_UNSUPPORTED;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(OT_BLOCK);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, A);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
     return e == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}
+
+template <int CPT, int R>
+static int launch_fused(SkArgs& A, int grid, cudaStream_t st) {
+    const int rows_max = (A.M + grid - 1) / grid;
+    const int nb_max = (rows_max + R - 1) / R;
+    const size_t band_bytes = (size_t)R * A.Ncol * sizeof(float);
+    A.rows_max = rows_max;
+    A.cols_max = (A.Ncol + grid - 1) / grid;
+    const size_t state = align256_hd(fused_rowstate_bytes(A.rows_max)) + fused_colstate_bytes(A.cols_max);
+    A.resident = (nb_max <= OT_MAX_STAGES && nb_max * band_bytes + state <= kSmemBudget) ? 1 : 0;
+    const int nstage = A.resident ? nb_max : 2;
+    const size_t smem = (size_t)nstage * band_bytes + state;
+    return coop_launch(sk_fused_kernel<CPT, R>, grid, st, smem, A, nstage);
+}
+
+template <int CPT, int R>
+static int launch_bulk_r(SkArgs& A, int grid, cudaStream_t st) {
+    A.rows_max = (A.M + grid - 1) / grid;
+    const int nb_max = (A.rows_max + R - 1) / R;
+    const size_t band_bytes = (size_t)R * A.Ncol * sizeof(float);
+    const size_t state = align256_hd((size_t)(A.Ncol + 2) * sizeof(double)) +
+                         align256_hd((size_t)3 * A.Ncol * sizeof(float)) + fused_rowstate_bytes(A.rows_max);
+    A.resident = (nb_max <= OT_MAX_STAGES && nb_max * band_bytes + state <= kSmemBudget) ? 1 : 0;
+    const int nstage = A.resident ? nb_max : 2;
+    const size_t smem = (size_t)nstage * band_bytes + state;
+    if (smem > 227 * 1024) return OT_ERR_UNSUPPORTED;
+    return coop_launch(sk_bulk_kernel<CPT, R>, grid, st, smem, A, nstage);
+}
+
+// One grid barrier per sweep (bulk FP64 reduce-add of the column sums).
+static int launch_bulk(SkArgs& A, int grid, cudaStream_t st) {
+    const int cpt = (A.Ncol + OT_BLOCK - 1) / OT_BLOCK;
+    const int rows_max = (A.M + grid - 1) / grid;
+    if (cpt <= 4) return rows_max <= 8 ? launch_bulk_r<4, 8>(A, grid, st) : launch_bulk_r<4, 16>(A, grid, st);
+    if (cpt <= 8) return launch_bulk_r<8, 8>(A, grid, st);
+    return launch_bulk_r<16, 4>(A, grid, st);
 }
 
 int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
     const bool stored = A.C != nullptr;
-    const bool fused = stored && A.Ncol <= kFusedMaxCols;
     const int grid = solver_grid(A.M);
     if (grid <= 0) return OT_ERR_CUDA;
-    const WsLayout L = ws_layout(A.M, A.Ncol, grid, fused);
+    const bool fused = fused_ok(A, grid);
+    const WsLayout L = ws_layout(A.M, A.Ncol, grid, stored && A.Ncol <= kFusedMaxCols);
     if (ws == nullptr || ws_bytes < L.total) return OT_ERR_WORKSPACE;
     if (((uintptr_t)ws) % 256 != 0) return OT_ERR_WORKSPACE;
     char* w = (char*)ws;
@@ -768,19 +1363,32 @@ int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
     A.cf = (float*)(w + L.cf);
     A.part = (float*)(w + L.part);
     A.l1part = (double*)(w + L.l1part);
+    A.queue = (unsigned*)(w + L.queue);
+    A.acc = (double*)(w + L.acc);
+    A.vstride = L.vstride;
     A.trace = (A.debug_flags & OT_DEBUG_TRACE) ? (unsigned long long*)(w + L.trace) : nullptr;
     A.pstride = L.pstride;
     if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return OT_ERR_CUDA;
+    if (fused && cudaMemsetAsync(A.acc, 0, sizeof(double) * 3 * OT_ACC_COPIES * (size_t)L.vstride, st) != cudaSuccess)
+        return OT_ERR_CUDA;
     if (!fused) {
-        return stored ? coop_launch(sk_twopass_kernel<false>, grid, A, st)
-                      : coop_launch(sk_twopass_kernel<true>, grid, A, st);
+        A.rows_max = (A.M + grid - 1) / grid;
+        const size_t smem = fused_rowstate_bytes(A.rows_max);
+        if (smem > kSmemBudget) return OT_ERR_UNSUPPORTED;
+        return stored ? coop_launch(sk_twopass_kernel<false>, grid, st, smem, A)
+                      : coop_launch(sk_twopass_kernel<true>, grid, st, smem, A);
     }
     const int cpt = (A.Ncol + OT_BLOCK - 1) / OT_BLOCK;
-    if (cpt <= 1) return coop_launch(sk_fused_kernel<1, 16>, grid, A, st);
-    if (cpt <= 2) return coop_launch(sk_fused_kernel<2, 16>, grid, A, st);
-    if (cpt <= 4) return coop_launch(sk_fused_kernel<4, 16>, grid, A, st);
-    if (cpt <= 8) return coop_launch(sk_fused_kernel<8, 8>, grid, A, st);
-    return coop_launch(sk_fused_kernel<16, 4>, grid, A, st);
+    // the cluster kernel updates every column in every block: worth it while Ncol <= 2048
+    // one barrier per sweep pays while the per-sweep column-sum vector is small
+    if (!(A.debug_flags & OT_DEBUG_NO_CLUSTER) && A.Ncol <= 2048) {
+        const int rc = launch_bulk(A, grid, st);
+        if (rc != OT_ERR_UNSUPPORTED) return rc;
+    }
+    const int rows_max = (A.M + grid - 1) / grid;
+    if (cpt <= 4) return rows_max <= 8 ? launch_fused<4, 8>(A, grid, st) : launch_fused<4, 16>(A, grid, st);
+    if (cpt <= 8) return launch_fused<8, 8>(A, grid, st);
+    return launch_fused<16, 4>(A, grid, st);
 }
 
 static bool opt_ok(const ot_options* o) {
@@ -832,6 +1440,7 @@ extern "C" int ot_sinkhorn_full(int n, const float* a, const float* b, const flo
                                 void* workspace, size_t ws_bytes, void* stream) {
     if (n <= 0 || !a || !b || !f || !g || !out || !opt_ok(opt)) return OT_ERR_ARG;
     if (!C && (!X || !Y)) return OT_ERR_ARG;
+    if (C && ((uintptr_t)C) % 16 != 0) return OT_ERR_ARG;
     SkArgs A = base_args(opt);
     A.M = n;
     A.Ncol = n;

@@ -46,6 +46,7 @@ OT_OP_VALUE_AND_GRAD = 2
 OT_OP_UNROLLED = 3
 OT_DEBUG_WITHHOLD_ARRIVAL = 1
 OT_DEBUG_TRACE = 2
+OT_DEBUG_NO_CLUSTER = 4
 
 EXPORTED = ("ot_version", "ot_status_string", "ot_workspace_bytes", "ot_fold_cost", "ot_sinkhorn_reduced",
             "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad")
@@ -161,7 +162,7 @@ def read_result(res: torch.Tensor) -> dict:
     r = ot_result.from_buffer_copy(raw)
     return {"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1, "marg_l2_col": r.marg_l2_col,
             "value": r.value, "transport_cost": r.transport_cost, "marg_l1_col": r.marg_l1_col,
-            "mass": r.reserved[0]}
+            "mass": r.reserved[0], "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass"}.get(r.reserved[1], "other")}
 
 
 def ot_workspace_bytes(op: int, m_or_n: int, N: int, opt: Optional[ot_options] = None) -> int:

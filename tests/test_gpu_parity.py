@@ -353,3 +353,25 @@ def test_warm_start_resume(cy):
     assert abs(r1["iters"] + r2["iters"] - r3["iters"]) <= 2
     d = host(w2) - host(w3)
     assert np.abs(d - d.mean()).max() < 1e-4 * p.max_cost
+
+
+def test_solver_variants_agree(cy):
+    """Bulk-reduce (one barrier per sweep), fused (two barriers) and two-pass solvers give the same iterate."""
+    p = I.image_grid_problem(side=32, seed=2, eps_frac=0.01)
+    Cb = dev(p.C_base)
+    G, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, p.m, p.N, C_base=Cb, eps=p.eps)
+    a, b = dev(p.a_base), dev(p.b_base)
+    w1, z1, o1 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps, tol=1e-6))
+    r1 = cy.read_result(o1)
+    w2, z2, o2 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G,
+                                        cy.options(p.eps, tol=1e-6, debug_flags=cy.OT_DEBUG_NO_CLUSTER))
+    r2 = cy.read_result(o2)
+    assert r1["variant"] == "bulk" and r2["variant"] == "fused"
+    assert abs(r1["iters"] - r2["iters"]) <= 1 and r1["status"] == r2["status"] == cy.OT_OK
+    d = host(w1) - host(w2)
+    assert np.abs(d - d.mean()).max() <= 1e-6 * p.max_cost
+    # odd size -> two-pass kernel on the same problem family
+    q = I.sector_problem(97, 3, seed=1, eps_frac=0.02)
+    Gq, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, q.m, q.N, C_base=dev(q.C_base), eps=q.eps)
+    _, _, o3 = cy.ot_sinkhorn_reduced(q.m, q.N, dev(q.a_base), dev(q.b_base), Gq, cy.options(q.eps, tol=1e-6))
+    assert cy.read_result(o3)["variant"] == "twopass"
