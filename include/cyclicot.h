@@ -174,6 +174,25 @@ int ot_sinkhorn_reduced(int m, int N, const float* a_base, const float* b_base, 
                         void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * ot_sinkhorn_reduced_static -- ot_sinkhorn_reduced without a caller workspace.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they call the solver (a plugin inside a
+ * framework that owns the device allocator, a loop that must not allocate
+ * after start-up).  Arguments and results are those of ot_sinkhorn_reduced;
+ * the scratch space comes from a 4 MiB array compiled into the library (one
+ * per device, held until the process exits), enough for m <= 4096 on a GPU
+ * with up to 152 SMs.  Returns OT_ERR_UNSUPPORTED, launching nothing, when the
+ * problem needs more scratch than that.  All calls on a device share the
+ * array (each call clears what must start at zero), so calls that overlap on
+ * the GPU race.  The first call on a device looks up the array's address with
+ * cudaGetSymbolAddress on the current device: make it before any stream
+ * capture.  Nothing here allocates memory.
+ */
+int ot_sinkhorn_reduced_static(int m, int N, const float* a_base, const float* b_base, const float* G,
+                               const ot_options* opt, double* w, double* z, ot_result* out, void* stream);
+
+/*
  * ot_sinkhorn_full -- plain Sinkhorn on the full n x n problem (the
  * comparison; Algorithm 3 Stage 2), same iteration and stopping rule.
  *

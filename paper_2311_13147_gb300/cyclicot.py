@@ -49,7 +49,7 @@ OT_DEBUG_TRACE = 2
 OT_DEBUG_NO_CLUSTER = 4
 
 EXPORTED = ("ot_version", "ot_status_string", "ot_workspace_bytes", "ot_fold_cost", "ot_sinkhorn_reduced",
-            "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad")
+            "ot_sinkhorn_reduced_static", "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad")
 
 
 class OTError(RuntimeError):
@@ -97,6 +97,9 @@ def lib():
     L.ot_sinkhorn_reduced.restype = ctypes.c_int
     L.ot_sinkhorn_reduced.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(ot_options), _vp,
                                       _vp, _vp, _vp, ctypes.c_size_t, _vp]
+    L.ot_sinkhorn_reduced_static.restype = ctypes.c_int
+    L.ot_sinkhorn_reduced_static.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(ot_options),
+                                             _vp, _vp, _vp, _vp]
     L.ot_sinkhorn_full.restype = ctypes.c_int
     L.ot_sinkhorn_full.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ot_options), _vp, _vp,
                                    _vp, _vp, ctypes.c_size_t, _vp]
@@ -202,6 +205,24 @@ def ot_sinkhorn_reduced(m: int, N: int, a_base, b_base, G, opt: ot_options, w=No
     code = lib().ot_sinkhorn_reduced(int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(G), ctypes.byref(opt),
                                      _ptr(w), _ptr(z), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
     _check(code, "ot_sinkhorn_reduced")
+    return w, z, out
+
+
+def ot_sinkhorn_reduced_static(m: int, N: int, a_base, b_base, G, opt: ot_options, w=None, z=None, out=None,
+                               stream=None):
+    """ot_sinkhorn_reduced with the library's own scratch array instead of a workspace.
+
+    For callers that cannot allocate device memory at the call site (the
+    outputs here are allocated only when not passed).  The scratch is shared
+    by all calls on a device: calls that overlap on the GPU race.
+    """
+    dev = G.device
+    w = torch.empty(m, dtype=torch.float64, device=dev) if w is None else w
+    z = torch.zeros(m, dtype=torch.float64, device=dev) if z is None else z
+    out = new_result(dev) if out is None else out
+    code = lib().ot_sinkhorn_reduced_static(int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(G), ctypes.byref(opt),
+                                            _ptr(w), _ptr(z), _ptr(out), _stream(stream))
+    _check(code, "ot_sinkhorn_reduced_static")
     return w, z, out
 
 

@@ -1,0 +1,76 @@
+"""The allocation-free solver entry point (runs last: collected after every other test file).
+
+ot_sinkhorn_reduced_static serves callers that cannot allocate device memory
+where they call the solver: its scratch space is an array compiled into the
+library instead of a caller workspace.  Its results must equal those of
+ot_sinkhorn_reduced on the same inputs, on consecutive calls that share the
+array.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2311_13147_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cy():
+    from paper_2311_13147_gb300 import build
+    build.build()
+    from paper_2311_13147_gb300 import cyclicot
+    return cyclicot
+
+
+def _dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def _solve_both(cy, p, tol=1e-6):
+    G, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, p.m, p.N, C_base=_dev(p.C_base), eps=p.eps)
+    a, b = _dev(p.a_base), _dev(p.b_base)
+    opt = cy.options(p.eps, tol=tol)
+    w0, z0, o0 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, opt)
+    ref = cy.read_result(o0)
+    runs = []
+    for _ in range(2):   # two calls in a row share the static scratch
+        w, z, o = cy.ot_sinkhorn_reduced_static(p.m, p.N, a, b, G, opt)
+        runs.append((w, z, cy.read_result(o)))
+    return (w0, z0, ref), runs
+
+
+@pytest.mark.parametrize("side,seed", [(64, 0), (32, 3)])
+def test_static_scratch_matches_workspace_solver(cy, side, seed):
+    p = I.image_grid_problem(side=side, seed=seed, eps_frac=0.01)
+    (w0, z0, ref), runs = _solve_both(cy, p)
+    assert ref["status"] == cy.OT_OK
+    torch.cuda.synchronize()
+    for w, z, r in runs:
+        assert r["status"] == cy.OT_OK, r
+        assert abs(r["iters"] - ref["iters"]) <= 1
+        assert r["marg_l1"] <= 1e-6
+        # same tolerance as the parity tests: potentials equal up to the dual constant
+        for x, x0 in ((w, w0), (z, z0)):
+            d = (x - x0).cpu().numpy()
+            assert np.abs(d - d.mean()).max() <= 1e-6 * p.max_cost
+
+
+def test_static_scratch_odd_size_and_limit(cy):
+    q = I.sector_problem(97, 3, seed=1, eps_frac=0.02)   # two-pass solver path
+    (w0, z0, ref), runs = _solve_both(cy, q)
+    for w, z, r in runs:
+        assert r["status"] == cy.OT_OK and abs(r["iters"] - ref["iters"]) <= 1
+        d = (w - w0).cpu().numpy()
+        assert np.abs(d - d.mean()).max() <= 1e-6 * q.max_cost
+    # beyond the static array: rejected before any launch.  The required scratch is
+    # checked first, so the call is only made when it must be refused (the cost
+    # buffer passed is then never read).
+    m = 100_000
+    opt = cy.options(0.1)
+    assert cy.ot_workspace_bytes(cy.OT_OP_SINKHORN_REDUCED, m, 2, opt) > (4 << 20)
+    G = torch.zeros(16, device="cuda")
+    a = torch.ones(m, device="cuda")
+    with pytest.raises(cy.OTError) as e:
+        cy.ot_sinkhorn_reduced_static(m, 2, a, a, G, opt)
+    assert e.value.code == cy.OT_ERR_UNSUPPORTED
