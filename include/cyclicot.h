@@ -250,6 +250,56 @@ int ot_value_and_grad(int m, int N, const float* a_base, const float* b_base,
                       float* d_a, float* d_b, float* d_C, float* d_x, float* d_y,
                       void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- batches of independent cyclic problems (uneven m and N) ------------ */
+
+/* One problem of a batch.  48 bytes. */
+typedef struct {
+    int m;              /* block size                                                      */
+    int N;              /* cyclic order                                                    */
+    float eps;          /* regulariser                                                     */
+    int ld;             /* row stride of its folded cost: multiple of 4, m <= ld <= 8192;
+                           the pad entries [m, ld) of each row must be finite (the fold
+                           writes 0)                                                       */
+    long long g_off;    /* offset (floats, multiple of 4) of its cost G [m][ld] in G_all    */
+    long long v_off;    /* offset (elements) of its vectors in a_all, b_all, w_all, z_all   */
+    long long x_off;    /* offset (points) of its base source points in the point buffer   */
+    long long y_off;    /* offset (points) of its base target points in the point buffer   */
+} ot_problem_desc;
+
+/* Workspace bytes of a batch of `count` problems with sum of m equal to total_m. */
+size_t ot_batch_workspace_bytes(int count, long long total_m);
+
+/*
+ * ot_batch_prepare -- copy the problem table into the workspace (outside any
+ * stream capture).  descs is HOST memory (count entries); it is not read
+ * after the call returns.  The prefix tables the solver needs are built here.
+ */
+int ot_batch_prepare(const ot_problem_desc* descs, int count, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * ot_batch_fold -- Eq. def_Kij soft-min fold for every problem of a prepared
+ * batch, cost from points: C_k[i][j] = |x_i - R^k y_j|^2, R the rotation by
+ * 2*pi/N (points: float2 array, offsets from the descriptors).  Writes each
+ * problem's G into G_all at g_off with row stride ld.
+ */
+int ot_batch_fold(int count, const float* points, float* G_all, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * ot_batch_solve -- cyclic Sinkhorn (Algorithm 2) on every problem of a
+ * prepared batch in ONE persistent cooperative launch (capturable in a CUDA
+ * graph: it only enqueues kernels and memsets).  Each sweep re-balances the
+ * rows of the still-active problems over the blocks; a problem leaves the
+ * batch when its full-scale row L1 error <= opt->tol_l1 (its state is then
+ * frozen) or after opt->max_iter iterations.  opt->eps is ignored (per
+ * problem eps in the descriptors).  Outputs per problem: w, z (mass-1/N
+ * convention, as ot_sinkhorn_reduced) at v_off, and results[p] (device array
+ * of `count` ot_result: iters, status, marg_l1).  total_m = max over problems
+ * of v_off + m (the length of the vector buffers), as given to prepare.
+ */
+int ot_batch_solve(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
+                   const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
+                   size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -312,3 +312,63 @@ def read_trace(ws: torch.Tensor) -> "np.ndarray":
     torch.cuda.synchronize()
     raw = ws[-256 * 8 * 8:].cpu().numpy().tobytes()
     return np.frombuffer(raw, dtype=np.uint64).reshape(256, 8).astype(np.int64)
+
+
+# ------------------------------------------------------------------ batches
+
+class ot_problem_desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("N", ctypes.c_int), ("eps", ctypes.c_float), ("ld", ctypes.c_int),
+                ("g_off", ctypes.c_longlong), ("v_off", ctypes.c_longlong), ("x_off", ctypes.c_longlong),
+                ("y_off", ctypes.c_longlong)]
+
+
+assert ctypes.sizeof(ot_problem_desc) == 48
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.ot_batch_workspace_bytes.restype = ctypes.c_size_t
+        L.ot_batch_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_longlong]
+        L.ot_batch_prepare.restype = ctypes.c_int
+        L.ot_batch_prepare.argtypes = [ctypes.POINTER(ot_problem_desc), ctypes.c_int, _vp, ctypes.c_size_t, _vp]
+        L.ot_batch_fold.restype = ctypes.c_int
+        L.ot_batch_fold.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.ot_batch_solve.restype = ctypes.c_int
+        L.ot_batch_solve.argtypes = [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.POINTER(ot_options),
+                                     _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L._batch_ready = True
+    return L
+
+
+def ot_batch_workspace_bytes(count: int, total_m: int) -> int:
+    return int(_batch_lib().ot_batch_workspace_bytes(int(count), int(total_m)))
+
+
+def ot_batch_prepare(descs, workspace_t, stream=None):
+    arr = (ot_problem_desc * len(descs))(*descs)
+    code = _batch_lib().ot_batch_prepare(arr, len(descs), _ptr(workspace_t), workspace_t.numel(), _stream(stream))
+    _check(code, "ot_batch_prepare")
+
+
+def ot_batch_fold(count: int, points, G_all, workspace_t, stream=None):
+    code = _batch_lib().ot_batch_fold(int(count), _ptr(points), _ptr(G_all), _ptr(workspace_t), workspace_t.numel(),
+                                      _stream(stream))
+    _check(code, "ot_batch_fold")
+
+
+def ot_batch_solve(count: int, total_m: int, G_all, a_all, b_all, opt: ot_options, w_all, z_all, results,
+                   workspace_t, stream=None):
+    code = _batch_lib().ot_batch_solve(int(count), int(total_m), _ptr(G_all), _ptr(a_all), _ptr(b_all),
+                                       ctypes.byref(opt), _ptr(w_all), _ptr(z_all), _ptr(results),
+                                       _ptr(workspace_t), workspace_t.numel(), _stream(stream))
+    _check(code, "ot_batch_solve")
+
+
+def read_results(res: torch.Tensor, count: int):
+    raw = bytes(res.cpu().numpy().tobytes())
+    out = []
+    for p in range(count):
+        r = ot_result.from_buffer_copy(raw[64 * p:64 * (p + 1)])
+        out.append({"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1})
+    return out

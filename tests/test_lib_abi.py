@@ -24,7 +24,8 @@ def libpath():
 def test_header_declares_the_boundary():
     names = declared_symbols()
     for n in ("ot_fold_cost", "ot_sinkhorn_reduced", "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad",
-              "ot_workspace_bytes", "ot_status_string", "ot_version"):
+              "ot_workspace_bytes", "ot_status_string", "ot_version", "ot_batch_prepare", "ot_batch_fold",
+              "ot_batch_solve", "ot_batch_workspace_bytes"):
         assert n in names
 
 
@@ -40,6 +41,9 @@ def test_host_only_entry_points(libpath):
     assert cy.status_string(cy.OT_ERR_TIMEOUT).startswith("OT_ERR_TIMEOUT")
     assert cy.status_string(12345) == "unknown status"
     assert ctypes.sizeof(cy.ot_result) == 64
+    assert ctypes.sizeof(cy.ot_problem_desc) == 48
+    assert cy.ot_batch_workspace_bytes(0, 8) == 0
+    assert cy.ot_batch_workspace_bytes(4, 100) > 0
 
 
 def test_binding_refuses_cpu_tensors(libpath):
@@ -54,8 +58,9 @@ def test_struct_layouts_match_header():
     """ot_options / ot_result field order in the binding follows the header."""
     from paper_2311_13147_gb300 import cyclicot as cy
     text = open(HEADER).read()
-    for struct, cls in (("ot_options", cy.ot_options), ("ot_result", cy.ot_result)):
+    for struct, cls in (("ot_options", cy.ot_options), ("ot_result", cy.ot_result),
+                        ("ot_problem_desc", cy.ot_problem_desc)):
         body = re.search(r"typedef struct \{([^{}]*)\} " + struct + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-        fields = re.findall(r"\b([a-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
+        fields = re.findall(r"\b([A-Za-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
         assert [f[0] for f in cls._fields_] == fields
