@@ -295,6 +295,11 @@ int ot_batch_fold(int count, const float* points, float* G_all, void* workspace,
  * convention, as ot_sinkhorn_reduced) at v_off, and results[p] (device array
  * of `count` ot_result: iters, status, marg_l1).  total_m = max over problems
  * of v_off + m (the length of the vector buffers), as given to prepare.
+ * G_all must be 16-byte aligned (cost rows are streamed with bulk copies);
+ * otherwise OT_ERR_ARG.  A copy or grid barrier that does not complete within
+ * opt->timeout_ns (0: 10 s) ends the launch with OT_ERR_TIMEOUT in every
+ * result (iters = -1).  The problems of one prepared workspace must not be
+ * solved on two streams at once.
  */
 int ot_batch_solve(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
                    const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,

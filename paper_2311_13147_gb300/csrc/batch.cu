@@ -36,7 +36,10 @@ int device_sms();
 #define OT_BATCH_MAXM 8192    // largest block size
 #define OT_BT 512             // threads per block
 #define OT_BW (OT_BT / 32)
-#define OT_BR 4               // rows per band
+#define OT_BV 4               // float4 column slots per thread and row
+#ifndef OT_STAGES
+#define OT_STAGES 3           // chunks in flight per block (bulk copies into shared memory)
+#endif
 
 struct BatchArgs {
     int count;
@@ -59,47 +62,45 @@ struct BatchArgs {
     int* active;                   // [count]
     int* iters;                    // [count]
     double* l1acc;                 // [2][count]
-    double* phi;                   // [2][total_m]
+    float* flo;                    // [2][total_m] row potential = fhi + flo (exactly), log2 units
     float* fhi;                    // [2][total_m]
-    float* frf;                    // [2][total_m]
+    float* frf;                    // [2][total_m] 2^flo
     double* gam;                   // [total_m]
     float* gc;                     // [total_m]
     float* cf;                     // [total_m]
     float* R;                      // [total_m] column sums
 };
 
-// Dynamic shared memory of the solver: problem table, prefix sums, active flags,
-// then three float vectors read as float4 (each offset a multiple of 16 bytes).
-constexpr size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+// Dynamic shared memory of the solver: OT_STAGES chunk stages (two rows per
+// group) filled by bulk copies, prefix sums, block sizes and active flags.
+constexpr size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 struct BatchSmem {
-    static constexpr size_t desc = 0;
-    static constexpr size_t pref = a16(desc + sizeof(ot_problem_desc) * OT_BATCH_MAX);
-    static constexpr size_t act = a16(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
-    static constexpr size_t gc = a16(act + sizeof(int) * OT_BATCH_MAX);
-    static constexpr size_t cf = a16(gc + sizeof(float) * OT_BATCH_MAXM);
-    static constexpr size_t acc = a16(cf + sizeof(float) * OT_BATCH_MAXM);
-    static constexpr size_t total = a16(acc + sizeof(float) * OT_BATCH_MAXM);
+    static constexpr size_t stage = 0;
+    static constexpr size_t pref = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES);
+    static constexpr size_t msz = a128(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
+    static constexpr size_t act = a128(msz + sizeof(int) * OT_BATCH_MAX);
+    static constexpr size_t total = a128(act + sizeof(int) * OT_BATCH_MAX);
 };
-static_assert(BatchSmem::gc % 16 == 0 && BatchSmem::cf % 16 == 0 && BatchSmem::acc % 16 == 0, "float4 alignment");
-static_assert(BatchSmem::total <= 227 * 1024, "shared memory");
+static_assert(4 * OT_BV * OT_BT == OT_BATCH_MAXM, "a full block covers the longest row");
+static_assert(BatchSmem::total + 2048 <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void red_add_f32(float* p, float v) {
     asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
-// Block-wide inclusive scan of OT_BATCH_MAX-bounded weights (one value per problem) into s_pref[0..count].
-__device__ void batch_prefix(const BatchArgs& A, const ot_problem_desc* sd, const int* act, bool rows,
-                             long long* s_pref, long long* s_wsum) {
+// Block-wide exclusive scan of the per-problem weights (m^2 for rows, m for
+// columns; 0 for finished problems) into s_pref[0..count].
+__device__ void batch_prefix(int count, const int* s_m, const int* act, bool rows, long long* s_pref,
+                             long long* s_wsum) {
     // each thread sums a contiguous chunk, then a warp scan of the chunk sums
     const int tid = threadIdx.x;
-    const int per = (A.count + OT_BT - 1) / OT_BT;
-    const int p0 = tid * per, p1 = min(A.count, p0 + per);
+    const int per = (count + OT_BT - 1) / OT_BT;
+    const int p0 = tid * per, p1 = min(count, p0 + per);
     long long loc = 0;
     for (int p = p0; p < p1; ++p) {
-        const long long m = sd[p].m;
+        const long long m = s_m[p];
         loc += act[p] ? (rows ? m * m : m) : 0;
     }
-    // block exclusive scan of loc
     const int lane = tid & 31, wid = tid >> 5;
     long long v = loc;
 #pragma unroll
@@ -122,10 +123,10 @@ __device__ void batch_prefix(const BatchArgs& A, const ot_problem_desc* sd, cons
     long long base = (wid > 0 ? s_wsum[wid - 1] : 0) + v - loc;
     for (int p = p0; p < p1; ++p) {
         s_pref[p] = base;
-        const long long m = sd[p].m;
+        const long long m = s_m[p];
         base += act[p] ? (rows ? m * m : m) : 0;
     }
-    if (tid == OT_BT - 1) s_pref[A.count] = base;
+    if (tid == OT_BT - 1) s_pref[count] = base;
     __syncthreads();
 }
 
@@ -140,33 +141,374 @@ __device__ __forceinline__ int find_problem(const long long* s_pref, int count, 
     return lo;
 }
 
-__global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    ot_problem_desc* sd = reinterpret_cast<ot_problem_desc*>(dsm + BatchSmem::desc);   // [count]
-    long long* s_pref = reinterpret_cast<long long*>(dsm + BatchSmem::pref);            // [count+1]
-    int* s_act = reinterpret_cast<int*>(dsm + BatchSmem::act);                          // [count]
-    float* s_gc = reinterpret_cast<float*>(dsm + BatchSmem::gc);                        // [MAXM]
-    float* s_cf = reinterpret_cast<float*>(dsm + BatchSmem::cf);                        // [MAXM]
-    float* s_acc = reinterpret_cast<float*>(dsm + BatchSmem::acc);                      // [MAXM]
-    __shared__ float s_red[OT_BR][OT_BW];
-    __shared__ float s_rowF[OT_BR];
-    __shared__ float s_rowU[OT_BR];
+// ---- thread groups of the row phase
+//
+// A problem segment is processed by groups of GS threads (GS = 32 .. 512, the
+// smallest power of two whose OT_BV float4 slots per thread cover the row
+// stride).  Thread gt of a group owns the float4 column slots gt + v * GS for
+// the whole segment, so its column contributions stay in registers until the
+// segment ends.  A group reduction is an xor butterfly inside each warp and,
+// for multi-warp groups, one named barrier and a butterfly over the warp
+// partials: every thread of the group obtains bit-identical row sums, so the
+// data-dependent branches below are uniform across the group.
+
+__device__ __forceinline__ void group_barrier(int gs, int q) {
+    if (gs > 32) asm volatile("bar.sync %0, %1;" ::"r"(q + 1), "r"(gs) : "memory");
+    else __syncwarp();
+}
+
+// All-reduce of two values (the two rows of a chunk) over a group.
+template <bool MAX>
+__device__ __forceinline__ void group_allreduce2(float& v0, float& v1, int gs, float* s_part, int& parity) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float a = __shfl_xor_sync(0xffffffffu, v0, o), b = __shfl_xor_sync(0xffffffffu, v1, o);
+        v0 = MAX ? fmaxf(v0, a) : v0 + a;
+        v1 = MAX ? fmaxf(v1, b) : v1 + b;
+    }
+    if (gs > 32) {
+        const int tid = threadIdx.x, lane = tid & 31, nw = gs >> 5, w0 = (tid >> 5) & ~(nw - 1);
+        if (lane == 0) {
+            s_part[(parity * OT_BW + (tid >> 5)) * 2] = v0;
+            s_part[(parity * OT_BW + (tid >> 5)) * 2 + 1] = v1;
+        }
+        group_barrier(gs, tid / gs);
+        const float id = MAX ? -INFINITY : 0.f;
+        float x0 = lane < nw ? s_part[(parity * OT_BW + w0 + lane) * 2] : id;
+        float x1 = lane < nw ? s_part[(parity * OT_BW + w0 + lane) * 2 + 1] : id;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float a = __shfl_xor_sync(0xffffffffu, x0, o), b = __shfl_xor_sync(0xffffffffu, x1, o);
+            x0 = MAX ? fmaxf(x0, a) : x0 + a;
+            x1 = MAX ? fmaxf(x1, b) : x1 + b;
+        }
+        v0 = x0;
+        v1 = x1;
+        parity ^= 1;   // the next reduction writes the other buffer (one barrier separates reuse)
+    }
+}
+
+struct SegCtx {
+    const float* Gp;
+    int gs, m, ld, ng4, r_lo, r_hi, t, cur, nxt;
+    long long v0, TM;
+    float kap, fisa;
+};
+
+// Per-row scalars of the previous iteration, loaded one chunk ahead.
+struct RowScalars {
+    float F;    // row potential (hi part)
+    float al;   // a_i (unnormalised)
+    float rf;   // 2^lo of the row potential
+};
+
+__device__ __forceinline__ void load_scalars(RowScalars& R, const BatchArgs& A, const SegCtx& X, int row) {
+    if (row >= X.r_hi) return;
+    const long long gi = X.v0 + row;
+    R.F = X.t > 1 ? A.fhi[X.cur * X.TM + gi] : 0.f;
+    R.al = A.a[gi];
+    R.rf = X.t > 1 ? A.frf[X.cur * X.TM + gi] : 1.f;
+}
+
+// The column data a thread owns for a whole segment: hi parts of the column
+// potentials and their lo factors (padding: -inf and 0).
+struct ColRegs {
+    float4 gc[OT_BV];
+    float4 cf[OT_BV];
+};
+
+__device__ __forceinline__ float4 exps4(const float4 c, const float4 gg, float kap, float F) {
+    return make_float4(ex2(fmaf(c.x, -kap, gg.x) + F), ex2(fmaf(c.y, -kap, gg.y) + F),
+                       ex2(fmaf(c.z, -kap, gg.z) + F), ex2(fmaf(c.w, -kap, gg.w) + F));
+}
+
+__device__ __forceinline__ float dot4(const float4 e, const float4 c, float s) {
+    return fmaf(e.x, c.x, fmaf(e.y, c.y, fmaf(e.z, c.z, fmaf(e.w, c.w, s))));
+}
+
+// Row update of the two rows of a chunk held by a group (Eq.
+// optimal_f_sinkhorn_logdomain in log2 units): S_r = sum_j 2^(gamma_j - kap c_rj + F_r)
+// around the previous potential F_r, new potential F_r - log2(S_r / alpha_r)
+// kept exactly as hi + lo, column contributions (alpha_r / S_r) e_rj added to
+// acc.  An explicit max shift is used on the first sweep and whenever a row
+// sum leaves the safe range.
+__device__ __forceinline__ void process_rows(const float* srow, const RowScalars (&R)[2], const BatchArgs& A,
+                                             const SegCtx& X, int row, int k, const ColRegs& CR, float* s_part,
+                                             int& parity, float4 (&acc)[OT_BV], float& l1) {
+    if (row >= X.r_hi) return;   // uniform over the group
+    const int GS = X.gs, gt = threadIdx.x & (GS - 1), nw = GS >> 5;
+    const bool two = row + 1 < X.r_hi;
+    // epilogue threads of the two rows: lane 0 of rotating warps (lanes 0 and 1 of a warp group)
+    const int ep0 = GS > 32 ? (((2 * k) % nw) << 5) : 0;
+    const int ep1 = GS > 32 ? (((2 * k + 1) % nw) << 5) : 1;
+    const float kap = X.kap;
+    const float al0 = R[0].al * X.fisa, al1 = R[1].al * X.fisa;
+    const float4* c0 = reinterpret_cast<const float4*>(srow);
+    const float4* c1 = reinterpret_cast<const float4*>(srow + X.ld);
+    float4 e0[OT_BV], e1[OT_BV];
+    float F0 = R[0].F, F1 = R[1].F, S0 = 0.f, S1 = 0.f;
+    bool shifted = X.t == 1;
+    if (!shifted) {
+#pragma unroll
+        for (int v = 0; v < OT_BV; ++v) {
+            const int g = gt + v * GS;
+            e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < X.ng4) {
+                e0[v] = exps4(c0[g], CR.gc[v], kap, F0);
+                S0 = dot4(e0[v], CR.cf[v], S0);
+                if (two) {
+                    e1[v] = exps4(c1[g], CR.gc[v], kap, F1);
+                    S1 = dot4(e1[v], CR.cf[v], S1);
+                }
+            }
+        }
+        group_allreduce2<false>(S0, S1, GS, s_part, parity);
+        if (gt == ep0) l1 += fabsf(fmaf(S0, R[0].rf - 1.0f, S0 - al0));
+        if (two && gt == ep1) l1 += fabsf(fmaf(S1, R[1].rf - 1.0f, S1 - al1));
+        // uniform over the group
+        shifted = !(S0 > 1e-30f && S0 < 1e30f) || (two && !(S1 > 1e-30f && S1 < 1e30f));
+    }
+    if (shifted) {
+        // explicit shifts F_r = -max_j (gamma_j - kap c_rj), both rows
+        float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+        for (int v = 0; v < OT_BV; ++v) {
+            const int g = gt + v * GS;
+            e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < X.ng4) {
+                const float4 gg = CR.gc[v];
+                float4 c = c0[g];
+                e0[v] = make_float4(fmaf(c.x, -kap, gg.x), fmaf(c.y, -kap, gg.y), fmaf(c.z, -kap, gg.z),
+                                    fmaf(c.w, -kap, gg.w));
+                m0 = fmaxf(m0, fmaxf(fmaxf(e0[v].x, e0[v].y), fmaxf(e0[v].z, e0[v].w)));
+                if (two) {
+                    c = c1[g];
+                    e1[v] = make_float4(fmaf(c.x, -kap, gg.x), fmaf(c.y, -kap, gg.y), fmaf(c.z, -kap, gg.z),
+                                        fmaf(c.w, -kap, gg.w));
+                    m1 = fmaxf(m1, fmaxf(fmaxf(e1[v].x, e1[v].y), fmaxf(e1[v].z, e1[v].w)));
+                }
+            }
+        }
+        group_allreduce2<true>(m0, m1, GS, s_part, parity);
+        F0 = m0 > -INFINITY ? -m0 : 0.f;
+        F1 = m1 > -INFINITY ? -m1 : 0.f;
+        S0 = S1 = 0.f;
+#pragma unroll
+        for (int v = 0; v < OT_BV; ++v) {
+            const int g = gt + v * GS;
+            if (g < X.ng4) {
+                float4 x = e0[v];
+                x = make_float4(ex2(x.x + F0), ex2(x.y + F0), ex2(x.z + F0), ex2(x.w + F0));
+                e0[v] = x;
+                S0 = dot4(x, CR.cf[v], S0);
+                if (two) {
+                    x = e1[v];
+                    x = make_float4(ex2(x.x + F1), ex2(x.y + F1), ex2(x.z + F1), ex2(x.w + F1));
+                    e1[v] = x;
+                    S1 = dot4(x, CR.cf[v], S1);
+                }
+            }
+        }
+        group_allreduce2<false>(S0, S1, GS, s_part, parity);
+    }
+    float u0 = 0.f, u1 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float S = r ? S1 : S0, F = r ? F1 : F0, al = r ? al1 : al0;
+        const int ep = r ? ep1 : ep0;
+        if (r == 1 && !two) break;
+        if (S > 1e-30f && S < 1e30f) {
+            if (r) u1 = __fdividef(al, S);
+            else u0 = __fdividef(al, S);
+            if (gt == ep) {
+                // new potential F - log2(S / alpha) held exactly as hi + lo (TwoSum)
+                const long long gi = X.v0 + row + r;
+                const float b = -lg2(__fdividef(S, al));
+                const float hi = __fadd_rn(F, b);
+                const float bv = __fsub_rn(hi, F);
+                const float lo = __fadd_rn(__fsub_rn(F, __fsub_rn(hi, bv)), __fsub_rn(b, bv));
+                A.fhi[X.nxt * X.TM + gi] = hi;
+                A.flo[X.nxt * X.TM + gi] = lo;
+                A.frf[X.nxt * X.TM + gi] = ex2(lo);
+            }
+        } else if (gt == ep) {
+            set_status(A.ctrl, OT_ERR_NONFINITE);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < OT_BV; ++v) {
+        acc[v].x = fmaf(u1, e1[v].x, fmaf(u0, e0[v].x, acc[v].x));
+        acc[v].y = fmaf(u1, e1[v].y, fmaf(u0, e0[v].y, acc[v].y));
+        acc[v].z = fmaf(u1, e1[v].z, fmaf(u0, e0[v].z, acc[v].z));
+        acc[v].w = fmaf(u1, e1[v].w, fmaf(u0, e0[v].w, acc[v].w));
+    }
+}
+
+// Pipeline state of a block: chunks are numbered in the order the block
+// consumes them (across segments and sweeps); chunk n uses stage n % OT_STAGES
+// and completes phase (n / OT_STAGES) & 1 of that stage's barrier.
+struct Pipe {
+    float* stage;                 // [OT_STAGES][2 * OT_BATCH_MAXM]
+    unsigned long long* full;     // [OT_STAGES]
+    long long consumed;           // chunks consumed so far
+    long long issued;             // chunks issued so far
+};
+
+// Chunk k of a segment: rows r_lo + 2 k NG .. (2 NG consecutive rows, two per
+// group), one bulk copy (rows are contiguous with stride ld; 16-byte multiples).
+__device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int NG, int k) {
+    const int r0 = X.r_lo + 2 * k * NG;
+    const int nr = min(2 * NG, X.r_hi - r0);
+    const unsigned bytes = (unsigned)nr * (unsigned)X.ld * 4u;
+    const int st = (int)(P.issued % OT_STAGES);
+    unsigned long long* bar = &P.full[st];
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(P.stage + (size_t)st * 2 * OT_BATCH_MAXM, X.Gp + (long long)r0 * X.ld, bytes, bar);
+    P.issued += 1;
+}
+
+// Rows [r_lo, r_hi) of one problem by all groups of the block.  Chunk k holds
+// rows r_lo + 2 (k NG + q) and the next one for group q; OT_STAGES chunks are in
+// flight.  Returns false (uniformly) if a copy did not complete in time.
+__device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p, int r_lo, int r_hi, int t,
+                             int GS, float* s_part, double isa, Pipe& P) {
+    const int NG = OT_BT / GS;
+    const int tid = threadIdx.x, gt = tid & (GS - 1), q = tid / GS;
+    SegCtx X;
+    X.Gp = A.G + d.g_off;
+    X.gs = GS;
+    X.m = d.m;
+    X.ld = d.ld;
+    X.ng4 = d.ld >> 2;
+    X.r_lo = r_lo;
+    X.r_hi = r_hi;
+    X.t = t;
+    X.cur = (t - 1) & 1;
+    X.nxt = X.cur ^ 1;
+    X.v0 = d.v_off;
+    X.TM = A.total_m;
+    X.kap = (float)(1.0 / ((double)d.eps * OT_LN2));
+    X.fisa = (float)isa;
+    const int nchunks = (r_hi - r_lo + 2 * NG - 1) / (2 * NG);
+    if (tid == 0) {
+        fence_proxy_async();
+        for (int k = 0; k < nchunks && k < OT_STAGES; ++k) issue_chunk(P, X, NG, k);
+    }
+    long long issued = P.consumed + min(nchunks, OT_STAGES);   // block-uniform copy of P.issued
+    // this thread's columns: 4 (gt + v GS) .. + 3
+    ColRegs CR;
+#pragma unroll
+    for (int v = 0; v < OT_BV; ++v) {
+        const int j = 4 * (gt + v * GS);
+        float gv[4], cv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const bool in = j + c < X.m;
+            gv[c] = in ? A.gc[X.v0 + j + c] : -INFINITY;
+            cv[c] = in ? A.cf[X.v0 + j + c] : 0.f;
+        }
+        CR.gc[v] = make_float4(gv[0], gv[1], gv[2], gv[3]);
+        CR.cf[v] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+    }
+    int parity = 0;
+    float4 acc[OT_BV];
+#pragma unroll
+    for (int v = 0; v < OT_BV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float l1 = 0.f;
+    RowScalars cur[2], nxt[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        cur[r].F = nxt[r].F = 0.f;
+        cur[r].al = nxt[r].al = 1.f;
+        cur[r].rf = nxt[r].rf = 1.f;
+        load_scalars(cur[r], A, X, r_lo + 2 * q + r);
+    }
+    bool ok = true;
+    for (int k = 0; k < nchunks; ++k) {
+        const int row = r_lo + 2 * (k * NG + q);
+        if (k + 1 < nchunks) {
+            load_scalars(nxt[0], A, X, row + 2 * NG);
+            load_scalars(nxt[1], A, X, row + 2 * NG + 1);
+        }
+        const int st = (int)(P.consumed % OT_STAGES);
+        const unsigned ph = (unsigned)((P.consumed / OT_STAGES) & 1);
+        const bool got = mbar_wait(&P.full[st], ph, A.timeout_ns);
+        // processed even after an expired wait (shared-memory reads stay in bounds), so
+        // that every thread of a group meets the group's barriers; the block then
+        // leaves together on the decision below
+        process_rows(P.stage + (size_t)st * 2 * OT_BATCH_MAXM + (size_t)(2 * q) * X.ld, cur, A, X, row, k, CR,
+                     s_part, parity, acc, l1);
+        // every thread has read the stage (its exponentials are in registers): refill it
+        if (__syncthreads_or(!got)) {
+            ok = false;
+            break;
+        }
+        P.consumed += 1;
+        if (k + OT_STAGES < nchunks) {
+            if (tid == 0) {
+                fence_proxy_async();
+                issue_chunk(P, X, NG, k + OT_STAGES);
+            }
+            issued += 1;
+        }
+        cur[0] = nxt[0];
+        cur[1] = nxt[1];
+    }
+    P.issued = issued;
+    if (!ok) return false;
+    // column contributions of this group (times the lo factors) and its L1 terms
+    if (r_lo + 2 * q < r_hi) {
+#pragma unroll
+        for (int v = 0; v < OT_BV; ++v) {
+            const int g = gt + v * GS;
+            if (g < X.ng4) {
+                const float4 cc = CR.cf[v];
+                const int j = 4 * g;
+                const long long o = X.v0 + j;
+                if (j < X.m) red_add_f32(A.R + o, acc[v].x * cc.x);
+                if (j + 1 < X.m) red_add_f32(A.R + o + 1, acc[v].y * cc.y);
+                if (j + 2 < X.m) red_add_f32(A.R + o + 2, acc[v].z * cc.z);
+                if (j + 3 < X.m) red_add_f32(A.R + o + 3, acc[v].w * cc.w);
+            }
+        }
+    }
+    if (l1 != 0.f) atomicAdd(A.l1acc + (size_t)(t & 1) * A.count + p, (double)l1);
+    return true;
+}
+
+__global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_constant__ BatchArgs A) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float* s_stage = reinterpret_cast<float*>(dsm + BatchSmem::stage);                 // [STAGES][2 MAXM]
+    long long* s_pref = reinterpret_cast<long long*>(dsm + BatchSmem::pref);           // [count+1]
+    int* s_m = reinterpret_cast<int*>(dsm + BatchSmem::msz);                           // [count]
+    int* s_act = reinterpret_cast<int*>(dsm + BatchSmem::act);                         // [count]
+    __shared__ float s_part[2 * OT_BW * 2];
     __shared__ long long s_wsum[32];
     __shared__ double s_dred[OT_BW];
-    __shared__ int s_flag;
+    __shared__ unsigned long long s_full[OT_STAGES];
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int B = blockIdx.x, Gd = gridDim.x;
     const int count = A.count;
     unsigned epoch = 0;
+    Pipe P;
+    P.stage = s_stage;
+    P.full = s_full;
+    P.consumed = 0;
+    P.issued = 0;
 
-    for (int p = tid; p < count; p += OT_BT) sd[p] = A.desc[p];
+    if (tid == 0) {
+        for (int st = 0; st < OT_STAGES; ++st) mbar_init(&s_full[st], 1);
+        fence_mbar_init();
+    }
+    for (int p = tid; p < count; p += OT_BT) s_m[p] = A.desc[p].m;
     __syncthreads();
 
     // ---- per-problem marginal sums and validation (problems split over blocks)
     for (int p = B; p < count; p += Gd) {
-        const int m = sd[p].m;
-        const long long v0 = sd[p].v_off;
+        const ot_problem_desc d = A.desc[p];
+        const int m = d.m;
+        const long long v0 = d.v_off;
         double sa = 0.0, sb = 0.0;
         int bad = 0;
         for (int i = tid; i < m; i += OT_BT) {
@@ -175,7 +517,6 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
             sa += x;
             sb += y;
         }
-        // block sums (OT_BW warps)
         sa = warp_sum(sa);
         sb = warp_sum(sb);
         bad = __syncthreads_or(bad);
@@ -208,7 +549,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
             }
         }
         // column potentials and sums
-        const float kap = (float)(1.0 / ((double)sd[p].eps * OT_LN2));
+        const float kap = (float)(1.0 / ((double)d.eps * OT_LN2));
         for (int j = tid; j < m; j += OT_BT) {
             const double g0 = A.warm ? A.z_out[v0 + j] * (double)kap : 0.0;
             const float hi = (float)g0;
@@ -221,12 +562,12 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
     if (!grid_sync(A.ctrl, Gd, A.timeout_ns, epoch)) goto fail;
 
     for (int t = 1;; ++t) {
-        const int cur = (t - 1) & 1, nxt = cur ^ 1;
+        const int nxt = t & 1;
         const long long TM = A.total_m;
         // ---------------- row phase
         for (int p = tid; p < count; p += OT_BT) s_act[p] = A.active[p];
         __syncthreads();
-        batch_prefix(A, sd, s_act, true, s_pref, s_wsum);
+        batch_prefix(count, s_m, s_act, true, s_pref, s_wsum);
         {
             // a row belongs to the block whose weight range holds the row's first entry
             const long long W = s_pref[count];
@@ -234,164 +575,34 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
             const int pfirst = (W > 0 && w0 < w1) ? find_problem(s_pref, count, w0) : count;
             for (int p = pfirst; p < count && s_pref[p] < w1; ++p) {
                 if (!s_act[p]) continue;
-                const int m = sd[p].m, ld = sd[p].ld;
+                const int m = s_m[p];
                 const long long base = s_pref[p];
                 const int r_lo = (w0 <= base) ? 0 : (int)((w0 - base + m - 1) / m);
                 const int r_hi = min(m, (int)((w1 - base + m - 1) / m));
                 if (r_lo >= r_hi) continue;
-                const float kap = (float)(1.0 / ((double)sd[p].eps * OT_LN2));
-                const long long v0 = sd[p].v_off;
-                const float* Gp = A.G + sd[p].g_off;
+                const ot_problem_desc d = A.desc[p];
+                const int ld = d.ld;
                 const double isa = A.inv_sa[p];
-                // stage this problem's column potentials; clear the accumulator
-                __syncthreads();
-                // padded columns [m, ld): gamma = -inf, factor 0 (their entries are exactly 0)
-                for (int j = tid; j < ld; j += OT_BT) {
-                    const bool v = j < m;
-                    s_gc[j] = v ? A.gc[v0 + j] : -INFINITY;
-                    s_cf[j] = v ? A.cf[v0 + j] : 0.f;
-                    s_acc[j] = 0.f;
+                // group size: the smallest power of two >= 32 whose OT_BV float4 slots cover the row
+                int gs = 32;
+                while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
+                if (!rows_segment(A, d, p, r_lo, r_hi, t, gs, s_part, isa, P)) {
+                    if (tid == 0) set_status(A.ctrl, OT_ERR_TIMEOUT);
+                    goto fail;
                 }
-                __syncthreads();
-                double l1 = 0.0;
-                const int ng4 = ld >> 2;   // ld % 4 == 0; the padded cost entries are finite (0)
-                for (int rb0 = r_lo; rb0 < r_hi; rb0 += OT_BR) {
-                    const int nr = min(OT_BR, r_hi - rb0);
-                    const bool safe = (t == 1);
-                    float F[OT_BR];
-#pragma unroll
-                    for (int r = 0; r < OT_BR; ++r)
-                        F[r] = (!safe && r < nr) ? A.fhi[cur * TM + v0 + rb0 + r] : 0.f;
-                    for (int attempt = 0; attempt < 2; ++attempt) {
-                        const bool shift = safe || attempt == 1;
-                        if (shift) {   // explicit max shift: F_r = -max_j (gamma_j - c_rj)
-                            float mx[OT_BR];
-#pragma unroll
-                            for (int r = 0; r < OT_BR; ++r) mx[r] = -INFINITY;
-                            for (int g = tid; g < ng4; g += OT_BT) {
-                                const float4 gg = reinterpret_cast<const float4*>(s_gc)[g];
-#pragma unroll
-                                for (int r = 0; r < OT_BR; ++r) {
-                                    if (r < nr) {
-                                        const float4 c = __ldg(reinterpret_cast<const float4*>(Gp + (long long)(rb0 + r) * ld) + g);
-                                        mx[r] = fmaxf(mx[r], fmaxf(fmaxf(fmaf(c.x, -kap, gg.x), fmaf(c.y, -kap, gg.y)),
-                                                                   fmaxf(fmaf(c.z, -kap, gg.z), fmaf(c.w, -kap, gg.w))));
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int r = 0; r < OT_BR; ++r) {
-                                const float t2 = warp_max(mx[r]);
-                                if (lane == 0) s_red[r][wid] = t2;
-                            }
-                            __syncthreads();
-                            if (tid < OT_BR) {
-                                float m2 = -INFINITY;
-                                for (int w2 = 0; w2 < OT_BW; ++w2) m2 = fmaxf(m2, s_red[tid][w2]);
-                                s_rowF[tid] = m2 > -INFINITY ? -m2 : 0.f;
-                            }
-                            __syncthreads();
-#pragma unroll
-                            for (int r = 0; r < OT_BR; ++r) F[r] = s_rowF[r];
-                        }
-                        // pass 1: row sums
-                        float s[OT_BR];
-#pragma unroll
-                        for (int r = 0; r < OT_BR; ++r) s[r] = 0.f;
-                        for (int g = tid; g < ng4; g += OT_BT) {
-                            const float4 gg = reinterpret_cast<const float4*>(s_gc)[g];
-                            const float4 cc = reinterpret_cast<const float4*>(s_cf)[g];
-#pragma unroll
-                            for (int r = 0; r < OT_BR; ++r) {
-                                if (r < nr) {
-                                    const float4 c = __ldg(reinterpret_cast<const float4*>(Gp + (long long)(rb0 + r) * ld) + g);
-                                    s[r] += ex2(fmaf(c.x, -kap, gg.x) + F[r]) * cc.x + ex2(fmaf(c.y, -kap, gg.y) + F[r]) * cc.y +
-                                            ex2(fmaf(c.z, -kap, gg.z) + F[r]) * cc.z + ex2(fmaf(c.w, -kap, gg.w) + F[r]) * cc.w;
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int r = 0; r < OT_BR; ++r) {
-                            const float t2 = warp_sum(s[r]);
-                            if (lane == 0) s_red[r][wid] = t2;
-                        }
-                        __syncthreads();
-                        if (tid == 0) s_flag = 0;
-                        __syncthreads();
-                        if (tid < nr) {
-                            const long long gi = v0 + rb0 + tid;
-                            float S = 0.f;
-                            for (int w2 = 0; w2 < OT_BW; ++w2) S += s_red[tid][w2];
-                            const float alpha = (float)((double)A.a[gi] * isa);
-                            if (!(S > 1e-30f && S < 1e30f)) {
-                                if (!shift) {
-                                    l1 += fabs((double)fmaf(S, A.frf[cur * TM + gi] - 1.0f, S - alpha));
-                                }
-                                s_flag = 1;
-                                s_rowU[tid] = 0.f;
-                            } else {
-                                double pnew;
-                                if (!shift) {
-                                    l1 += fabs((double)fmaf(S, A.frf[cur * TM + gi] - 1.0f, S - alpha));
-                                    pnew = (double)F[tid] - (double)lg2(__fdividef(S, alpha));
-                                } else {
-                                    pnew = (double)F[tid] - (double)lg2(__fdividef(S, alpha));
-                                }
-                                const float hi = (float)pnew;
-                                A.phi[nxt * TM + gi] = pnew;
-                                A.fhi[nxt * TM + gi] = hi;
-                                A.frf[nxt * TM + gi] = ex2((float)(pnew - (double)hi));
-                                s_rowU[tid] = __fdividef(alpha, S);
-                            }
-                        }
-                        if (tid >= nr && tid < OT_BR) s_rowU[tid] = 0.f;
-                        __syncthreads();
-                        if (!s_flag) break;
-                        if (attempt == 1 && tid == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
-                        __syncthreads();
-                    }
-                    // pass 2: column contributions (second read of the band)
-                    float U[OT_BR];
-#pragma unroll
-                    for (int r = 0; r < OT_BR; ++r) U[r] = s_rowU[r];
-                    for (int g = tid; g < ng4; g += OT_BT) {
-                        const float4 gg = reinterpret_cast<const float4*>(s_gc)[g];
-                        const float4 cc = reinterpret_cast<const float4*>(s_cf)[g];
-                        float4 ac = reinterpret_cast<float4*>(s_acc)[g];
-#pragma unroll
-                        for (int r = 0; r < OT_BR; ++r) {
-                            if (r < nr) {
-                                const float4 c = __ldg(reinterpret_cast<const float4*>(Gp + (long long)(rb0 + r) * ld) + g);
-                                ac.x = fmaf(U[r], ex2(fmaf(c.x, -kap, gg.x) + F[r]) * cc.x, ac.x);
-                                ac.y = fmaf(U[r], ex2(fmaf(c.y, -kap, gg.y) + F[r]) * cc.y, ac.y);
-                                ac.z = fmaf(U[r], ex2(fmaf(c.z, -kap, gg.z) + F[r]) * cc.z, ac.z);
-                                ac.w = fmaf(U[r], ex2(fmaf(c.w, -kap, gg.w) + F[r]) * cc.w, ac.w);
-                            }
-                        }
-                        reinterpret_cast<float4*>(s_acc)[g] = ac;
-                    }
-                    __syncthreads();
-                }
-                // flush the segment's column contributions and L1 terms
-                for (int j = tid; j < m; j += OT_BT) {
-                    const float v = s_acc[j];
-                    if (v != 0.f) red_add_f32(A.R + v0 + j, v);
-                }
-                l1 = warp_sum(l1);   // only lanes < OT_BR of warp 0 hold terms
-                if (tid == 0 && l1 != 0.0) atomicAdd(A.l1acc + (size_t)(t & 1) * count + p, l1);
             }
         }
         if (!grid_sync(A.ctrl, Gd, A.timeout_ns, epoch)) goto fail;
 
         // ---------------- column phase
-        batch_prefix(A, sd, s_act, false, s_pref, s_wsum);
+        batch_prefix(count, s_m, s_act, false, s_pref, s_wsum);
         {
             const long long W = s_pref[count];
             const long long c0 = W * B / Gd, c1 = W * (B + 1) / Gd;
             for (long long cidx = c0 + tid; cidx < c1; cidx += OT_BT) {
                 const int p = find_problem(s_pref, count, cidx);
                 const int j = (int)(cidx - s_pref[p]);
-                const long long v0 = sd[p].v_off;
+                const long long v0 = A.desc[p].v_off;
                 const double L1 = A.l1acc[(size_t)(t & 1) * count + p];
                 const int done = t - 1;
                 int st = -1;
@@ -424,9 +635,10 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
                     gnew = A.gam[v0 + j] - (double)lg2(__fdividef(Rj, (float)beta));
                 } else {
                     // rare: recompute the column's log-sum-exp with an explicit max (one thread)
-                    const int m = sd[p].m, ld = sd[p].ld;
-                    const float kap = (float)(1.0 / ((double)sd[p].eps * OT_LN2));
-                    const float* Gp = A.G + sd[p].g_off;
+                    const ot_problem_desc d = A.desc[p];
+                    const int m = d.m, ld = d.ld;
+                    const float kap = (float)(1.0 / ((double)d.eps * OT_LN2));
+                    const float* Gp = A.G + d.g_off;
                     float mx = -INFINITY, s = 0.f;
                     for (int i = 0; i < m; ++i) {
                         const float x = fmaf(Gp[(long long)i * ld + j], -kap, A.fhi[nxt * TM + v0 + i]);
@@ -454,69 +666,85 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(BatchArgs A) {
 
     // ---------------- outputs: each block writes a share of all problems
     for (int p = B; p < count; p += Gd) {
-        const int m = sd[p].m;
-        const long long v0 = sd[p].v_off;
+        const ot_problem_desc d = A.desc[p];
+        const int m = d.m;
+        const long long v0 = d.v_off;
         const int it = A.iters[p];
         const int buf = it & 1;
-        const double unit = (double)sd[p].eps * OT_LN2;
-        const double shift = -(double)sd[p].eps * log((double)sd[p].N);
+        const double unit = (double)d.eps * OT_LN2;
+        const double shift = -(double)d.eps * log((double)d.N);
         for (int i = tid; i < m; i += OT_BT) {
             // a problem rejected by the validation gets NaN potentials
-            A.w_out[v0 + i] = it < 0 ? (double)NAN : A.phi[(size_t)buf * A.total_m + v0 + i] * unit + shift;
+            const size_t o = (size_t)buf * A.total_m + v0 + i;
+            A.w_out[v0 + i] = it < 0 ? (double)NAN : ((double)A.fhi[o] + (double)A.flo[o]) * unit + shift;
             A.z_out[v0 + i] = it < 0 ? (double)NAN : A.gam[v0 + i] * unit;
         }
         if (tid == 0) A.res[p].reserved[1] = 4.0;   // variant code: batch
     }
     return;
 fail:
-    if (threadIdx.x == 0) {
+    // no copy may still be writing into this block's shared memory when it exits
+    if (tid == 0) {
+        for (long long u = P.consumed; u < P.issued; ++u)
+            if (!mbar_wait(&s_full[u % OT_STAGES], (unsigned)((u / OT_STAGES) & 1), A.timeout_ns)) break;
         for (int p = B; p < count; p += Gd) {
             A.res[p].iters = -1;
             A.res[p].status = ld_volatile_int(&A.ctrl->status);
         }
     }
+    __syncthreads();
 }
 
 // ---- batched fold from points: G_p[i][j] = -eps log sum_k exp(-|x_i - R^k y_j|^2 / eps)
+// (Eq. def_Kij with the squared Euclidean cost of rotated points).  Blocks take
+// rows; |x_i - R^k y_j| = |R^-k x_i - y_j|, so the N rotations of x_i are formed
+// once per row in shared memory and each thread streams columns j.
 __global__ void __launch_bounds__(256) batch_fold_kernel(const ot_problem_desc* desc, int count,
                                                          const float2* pts, float* G_all) {
     const int p = blockIdx.y;
     if (p >= count) return;
     const ot_problem_desc d = desc[p];
     __shared__ float2 rot[256];
+    __shared__ float2 xr[256];
     for (int k = threadIdx.x; k < d.N && k < 256; k += blockDim.x) {
         float sn, cs;
         sincospif(2.0f * (float)k / (float)d.N, &sn, &cs);
         rot[k] = make_float2(cs, sn);
     }
-    __syncthreads();
     const float kap = (float)(1.0 / ((double)d.eps * OT_LN2));
-    const long long mm = (long long)d.m * d.ld;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / d.ld), j = (int)(e - (long long)i * d.ld);
-        if (j >= d.m) {   // row padding: a finite value (the solver gives these columns zero weight)
-            G_all[d.g_off + (long long)i * d.ld + j] = 0.f;
-            continue;
+    const float inv_kap = (float)((double)d.eps * OT_LN2);
+    for (int i = blockIdx.x; i < d.m; i += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x < d.N) {   // R^-k x_i
+            const float2 r = rot[threadIdx.x], xi = pts[d.x_off + i];
+            xr[threadIdx.x] = make_float2(fmaf(r.x, xi.x, r.y * xi.y), fmaf(r.x, xi.y, -r.y * xi.x));
         }
-        const float2 xi = pts[d.x_off + i], yj = pts[d.y_off + j];
-        float mn = 0.f, s = 1.f;
-        for (int k = 0; k < d.N; ++k) {
-            const float2 r = rot[k];
-            const float yx = r.x * yj.x - r.y * yj.y, yy = r.y * yj.x + r.x * yj.y;
-            const float dx = xi.x - yx, dy = xi.y - yy;
-            const float c = fmaf(dx, dx, dy * dy);
-            if (k == 0) mn = c;
-            else if (c < mn) { s = fmaf(s, ex2((c - mn) * kap), 1.0f); mn = c; }
-            else s += ex2((mn - c) * kap);
+        __syncthreads();
+        float* Grow = G_all + d.g_off + (long long)i * d.ld;
+        for (int j = threadIdx.x; j < d.ld; j += blockDim.x) {
+            if (j >= d.m) {   // row padding: a finite value (the solver gives these columns zero weight)
+                Grow[j] = 0.f;
+                continue;
+            }
+            const float2 yj = pts[d.y_off + j];
+            float mn = 0.f, s = 1.f;
+            for (int k = 0; k < d.N; ++k) {
+                const float2 xk = xr[k];
+                const float dx = xk.x - yj.x, dy = xk.y - yj.y;
+                const float c = fmaf(dx, dx, dy * dy);
+                if (k == 0) mn = c;
+                else if (c < mn) { s = fmaf(s, ex2((c - mn) * kap), 1.0f); mn = c; }
+                else s += ex2((mn - c) * kap);
+            }
+            Grow[j] = mn - lg2(s) * inv_kap;
         }
-        G_all[d.g_off + (long long)i * d.ld + j] = mn - lg2(s) / kap;
     }
 }
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchLayout {
-    size_t ctrl, desc, inv_sa, inv_sb, active, iters, l1acc, phi, fhi, frf, gam, gc, cf, R, total;
+    size_t ctrl, desc, inv_sa, inv_sb, active, iters, l1acc, flo, fhi, frf, gam, gc, cf, R, total;
 };
 
 static BatchLayout batch_layout(int count, long long TM) {
@@ -529,7 +757,7 @@ static BatchLayout batch_layout(int count, long long TM) {
     L.active = o; o = a256(o + sizeof(int) * (size_t)count);
     L.iters = o; o = a256(o + sizeof(int) * (size_t)count);
     L.l1acc = o; o = a256(o + sizeof(double) * 2 * (size_t)count);
-    L.phi = o; o = a256(o + sizeof(double) * 2 * (size_t)TM);
+    L.flo = o; o = a256(o + sizeof(float) * 2 * (size_t)TM);
     L.fhi = o; o = a256(o + sizeof(float) * 2 * (size_t)TM);
     L.frf = o; o = a256(o + sizeof(float) * 2 * (size_t)TM);
     L.gam = o; o = a256(o + sizeof(double) * (size_t)TM);
@@ -598,7 +826,7 @@ extern "C" int ot_batch_fold(int count, const float* points, float* G_all, void*
     const BatchLayout L = batch_layout(count, 1);
     const ot_problem_desc* d = (const ot_problem_desc*)((char*)workspace + a256(sizeof(BatchHeader)) + L.desc);
     (void)ws_bytes;
-    dim3 grid(64u, (unsigned)count);   // blocks of small problems leave early
+    dim3 grid(64u, (unsigned)count);   // blocks beyond a problem's rows leave at once
     batch_fold_kernel<<<grid, 256, 0, st>>>(d, count, (const float2*)points, G_all);
     return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
 }
@@ -610,6 +838,7 @@ extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, 
         !z_all || !results || !workspace)
         return OT_ERR_ARG;
     if (opt->max_iter < 1 || opt->tol_l1 < 0.0) return OT_ERR_ARG;
+    if (((uintptr_t)G_all) % 16) return OT_ERR_ARG;   // bulk copies of cost rows need 16-byte alignment
     if (ws_bytes < ot_batch_workspace_bytes(count, total_m) || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char* base = (char*)workspace + a256(sizeof(BatchHeader));
@@ -635,7 +864,7 @@ extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, 
     A.active = (int*)(base + L.active);
     A.iters = (int*)(base + L.iters);
     A.l1acc = (double*)(base + L.l1acc);
-    A.phi = (double*)(base + L.phi);
+    A.flo = (float*)(base + L.flo);
     A.fhi = (float*)(base + L.fhi);
     A.frf = (float*)(base + L.frf);
     A.gam = (double*)(base + L.gam);
