@@ -85,7 +85,7 @@ typedef struct {
     int precision;                  /* OT_FP32_LOG (the only value ot_sinkhorn_* take)     */
     int warm_start;                 /* 1: start from the g passed in (f is recomputed)     */
     unsigned long long timeout_ns;  /* limit of each device-side wait; 0 = 10 s            */
-    int tile_override;              /* reserved, must be 0                                 */
+    int tile_override;              /* 0; batch solver: a configuration code (autotune)    */
     int debug_flags;                /* 0 in normal use.
                                        bit 0 (OT_DEBUG_WITHHOLD_ARRIVAL), fault injection:
                                        block 0 never arrives at the first grid barrier,
@@ -295,6 +295,11 @@ int ot_batch_fold(int count, const float* points, float* G_all, void* workspace,
  * convention, as ot_sinkhorn_reduced) at v_off, and results[p] (device array
  * of `count` ot_result: iters, status, marg_l1).  total_m = max over problems
  * of v_off + m (the length of the vector buffers), as given to prepare.
+ * opt->tile_override selects a launch configuration: 0 = default (3-stage
+ * pipeline, tight thread groups, convergence tested every opt->check_every
+ * iterations), or a code returned by ot_batch_autotune (1..12).  With a
+ * cadence k > 1 a problem stops at the first multiple of k whose state meets
+ * the tolerance.
  * G_all must be 16-byte aligned (cost rows are streamed with bulk copies);
  * otherwise OT_ERR_ARG.  A copy or grid barrier that does not complete within
  * opt->timeout_ns (0: 10 s) ends the launch with OT_ERR_TIMEOUT in every
@@ -304,6 +309,24 @@ int ot_batch_fold(int count, const float* points, float* G_all, void* workspace,
 int ot_batch_solve(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
                    const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
                    size_t ws_bytes, void* stream);
+
+/*
+ * ot_batch_autotune -- choose the batch solver's launch configuration for a
+ * prepared batch on the current device (no counterpart in the paper: an
+ * implementation choice).  Times, on `stream`, the pipeline depth x group-size
+ * policy candidates over 4 full sweeps, then the convergence-check cadences
+ * 1, 2, 4 with complete solves under opt's tolerance; returns the fastest code
+ * in *config_out (pass it as ot_options.tile_override to ot_batch_solve).
+ * ms_out (host, 7 floats, may be NULL) receives the measured times.  The
+ * result is cached per (device, problem table, tol, max_iter): a repeated call
+ * returns the cached code without launching anything.  Otherwise the outputs
+ * (w, z, results) are those of a complete solve with the chosen code.  Blocks
+ * the calling thread; must not be called while `stream` is being captured
+ * (OT_ERR_ARG).
+ */
+int ot_batch_autotune(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
+                      const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
+                      size_t ws_bytes, void* stream, int* config_out, float* ms_out);
 
 #ifdef __cplusplus
 }

@@ -4,8 +4,9 @@ Packs a list of problems (block size m, order N, eps, base points and
 marginals) into the flat device buffers the C ABI expects -- descriptors,
 one float2 point buffer, one cost buffer with 4-aligned rows, one vector
 buffer per marginal / potential -- and runs ot_batch_fold + ot_batch_solve
-(one persistent launch each).  ``BatchSolver.capture()`` records the fold and
-the solve in a CUDA graph that ``replay()`` launches again.
+(one persistent launch each).  ``BatchSolver.autotune()`` picks the solver's
+launch configuration for the batch; ``BatchSolver.capture()`` records the fold
+and the solve in a CUDA graph that ``replay()`` launches again.
 """
 from __future__ import annotations
 
@@ -58,6 +59,15 @@ class BatchSolver:
     def run(self):
         self.fold()
         self.solve()
+
+    def autotune(self):
+        """Pick the launch configuration for this batch (cached per device and problem table)."""
+        self.opt.tile_override = 0
+        code, ms = cy.ot_batch_autotune(self.count, self.total_m, self.G, self.a, self.b, self.opt, self.w, self.z,
+                                        self.res, self.ws)
+        self.opt.tile_override = code
+        self.tuning_ms = ms
+        return code
 
     def capture(self):
         """Record fold + solve in a CUDA graph (after one eager run, outside capture)."""

@@ -26,6 +26,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 
 namespace cyc {
@@ -37,9 +42,8 @@ int device_sms();
 #define OT_BT 512             // threads per block
 #define OT_BW (OT_BT / 32)
 #define OT_BV 4               // float4 column slots per thread and row
-#ifndef OT_STAGES
-#define OT_STAGES 3           // chunks in flight per block (bulk copies into shared memory)
-#endif
+#define OT_STAGES_MAX 3       // chunks in flight per block (bulk copies into shared memory)
+#define OT_BATCH_NCFG 12      // tunable launch configurations (see decode_cfg)
 
 struct BatchArgs {
     int count;
@@ -51,6 +55,8 @@ struct BatchArgs {
     int max_iter;
     unsigned long long timeout_ns;
     int warm;
+    int gs_shift;                  // group-size policy (0: tight, 1: one size larger)
+    int check_every;               // the stopping rule is applied every check_every iterations
     double* w_out;
     double* z_out;
     ot_result* res;
@@ -71,12 +77,12 @@ struct BatchArgs {
     float* R;                      // [total_m] column sums
 };
 
-// Dynamic shared memory of the solver: OT_STAGES chunk stages (two rows per
+// Dynamic shared memory of the solver: up to OT_STAGES_MAX chunk stages (two rows per
 // group) filled by bulk copies, prefix sums, block sizes and active flags.
 constexpr size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 struct BatchSmem {
     static constexpr size_t stage = 0;
-    static constexpr size_t pref = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES);
+    static constexpr size_t pref = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES_MAX);
     static constexpr size_t msz = a128(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
     static constexpr size_t act = a128(msz + sizeof(int) * OT_BATCH_MAX);
     static constexpr size_t total = a128(act + sizeof(int) * OT_BATCH_MAX);
@@ -345,22 +351,23 @@ __device__ __forceinline__ void process_rows(const float* srow, const RowScalars
 }
 
 // Pipeline state of a block: chunks are numbered in the order the block
-// consumes them (across segments and sweeps); chunk n uses stage n % OT_STAGES
-// and completes phase (n / OT_STAGES) & 1 of that stage's barrier.
+// consumes them (across segments and sweeps); chunk n uses stage n % STAGES
+// and completes phase (n / STAGES) & 1 of that stage's barrier.
 struct Pipe {
-    float* stage;                 // [OT_STAGES][2 * OT_BATCH_MAXM]
-    unsigned long long* full;     // [OT_STAGES]
+    float* stage;                 // [STAGES][2 * OT_BATCH_MAXM]
+    unsigned long long* full;     // [STAGES]
     long long consumed;           // chunks consumed so far
     long long issued;             // chunks issued so far
 };
 
 // Chunk k of a segment: rows r_lo + 2 k NG .. (2 NG consecutive rows, two per
 // group), one bulk copy (rows are contiguous with stride ld; 16-byte multiples).
+template <int STAGES>
 __device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int NG, int k) {
     const int r0 = X.r_lo + 2 * k * NG;
     const int nr = min(2 * NG, X.r_hi - r0);
     const unsigned bytes = (unsigned)nr * (unsigned)X.ld * 4u;
-    const int st = (int)(P.issued % OT_STAGES);
+    const int st = (int)(P.issued % STAGES);
     unsigned long long* bar = &P.full[st];
     mbar_arrive_expect_tx(bar, bytes);
     bulk_g2s(P.stage + (size_t)st * 2 * OT_BATCH_MAXM, X.Gp + (long long)r0 * X.ld, bytes, bar);
@@ -368,8 +375,9 @@ __device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int NG, in
 }
 
 // Rows [r_lo, r_hi) of one problem by all groups of the block.  Chunk k holds
-// rows r_lo + 2 (k NG + q) and the next one for group q; OT_STAGES chunks are in
+// rows r_lo + 2 (k NG + q) and the next one for group q; STAGES chunks are in
 // flight.  Returns false (uniformly) if a copy did not complete in time.
+template <int STAGES>
 __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p, int r_lo, int r_hi, int t,
                              int GS, float* s_part, double isa, Pipe& P) {
     const int NG = OT_BT / GS;
@@ -390,11 +398,12 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     X.kap = (float)(1.0 / ((double)d.eps * OT_LN2));
     X.fisa = (float)isa;
     const int nchunks = (r_hi - r_lo + 2 * NG - 1) / (2 * NG);
+    // (no proxy fence before a refill: a stage's previous contents were only read
+    // through the generic proxy, and a block barrier orders those reads first)
     if (tid == 0) {
-        fence_proxy_async();
-        for (int k = 0; k < nchunks && k < OT_STAGES; ++k) issue_chunk(P, X, NG, k);
+        for (int k = 0; k < nchunks && k < STAGES; ++k) issue_chunk<STAGES>(P, X, NG, k);
     }
-    long long issued = P.consumed + min(nchunks, OT_STAGES);   // block-uniform copy of P.issued
+    long long issued = P.consumed + min(nchunks, STAGES);   // block-uniform copy of P.issued
     // this thread's columns: 4 (gt + v GS) .. + 3
     ColRegs CR;
 #pragma unroll
@@ -430,8 +439,8 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
             load_scalars(nxt[0], A, X, row + 2 * NG);
             load_scalars(nxt[1], A, X, row + 2 * NG + 1);
         }
-        const int st = (int)(P.consumed % OT_STAGES);
-        const unsigned ph = (unsigned)((P.consumed / OT_STAGES) & 1);
+        const int st = (int)(P.consumed % STAGES);
+        const unsigned ph = (unsigned)((P.consumed / STAGES) & 1);
         const bool got = mbar_wait(&P.full[st], ph, A.timeout_ns);
         // processed even after an expired wait (shared-memory reads stay in bounds), so
         // that every thread of a group meets the group's barriers; the block then
@@ -444,11 +453,8 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
             break;
         }
         P.consumed += 1;
-        if (k + OT_STAGES < nchunks) {
-            if (tid == 0) {
-                fence_proxy_async();
-                issue_chunk(P, X, NG, k + OT_STAGES);
-            }
+        if (k + STAGES < nchunks) {
+            if (tid == 0) issue_chunk<STAGES>(P, X, NG, k + STAGES);
             issued += 1;
         }
         cur[0] = nxt[0];
@@ -476,6 +482,7 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     return true;
 }
 
+template <int STAGES>
 __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(128) unsigned char dsm[];
     float* s_stage = reinterpret_cast<float*>(dsm + BatchSmem::stage);                 // [STAGES][2 MAXM]
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
     __shared__ float s_part[2 * OT_BW * 2];
     __shared__ long long s_wsum[32];
     __shared__ double s_dred[OT_BW];
-    __shared__ unsigned long long s_full[OT_STAGES];
+    __shared__ unsigned long long s_full[STAGES];
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int B = blockIdx.x, Gd = gridDim.x;
@@ -498,7 +505,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
     P.issued = 0;
 
     if (tid == 0) {
-        for (int st = 0; st < OT_STAGES; ++st) mbar_init(&s_full[st], 1);
+        for (int st = 0; st < STAGES; ++st) mbar_init(&s_full[st], 1);
         fence_mbar_init();
     }
     for (int p = tid; p < count; p += OT_BT) s_m[p] = A.desc[p].m;
@@ -586,7 +593,8 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 // group size: the smallest power of two >= 32 whose OT_BV float4 slots cover the row
                 int gs = 32;
                 while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
-                if (!rows_segment(A, d, p, r_lo, r_hi, t, gs, s_part, isa, P)) {
+                gs = min(OT_BT, gs << A.gs_shift);   // tuned: a larger group takes fewer slots per thread
+                if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, isa, P)) {
                     if (tid == 0) set_status(A.ctrl, OT_ERR_TIMEOUT);
                     goto fail;
                 }
@@ -607,8 +615,9 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 const int done = t - 1;
                 int st = -1;
                 if (done >= 1) {
-                    if (L1 != L1) st = OT_ERR_NONFINITE;
-                    else if (L1 <= A.tol) st = OT_OK;
+                    const bool check = done % A.check_every == 0;
+                    if (check && L1 != L1) st = OT_ERR_NONFINITE;
+                    else if (check && L1 <= A.tol) st = OT_OK;
                     else if (done >= A.max_iter) st = OT_ERR_NOT_CONVERGED;
                 }
                 const float Rj = A.R[v0 + j];
@@ -686,7 +695,7 @@ fail:
     // no copy may still be writing into this block's shared memory when it exits
     if (tid == 0) {
         for (long long u = P.consumed; u < P.issued; ++u)
-            if (!mbar_wait(&s_full[u % OT_STAGES], (unsigned)((u / OT_STAGES) & 1), A.timeout_ns)) break;
+            if (!mbar_wait(&s_full[u % STAGES], (unsigned)((u / STAGES) & 1), A.timeout_ns)) break;
         for (int p = B; p < count; p += Gd) {
             A.res[p].iters = -1;
             A.res[p].status = ld_volatile_int(&A.ctrl->status);
@@ -831,16 +840,65 @@ extern "C" int ot_batch_fold(int count, const float* points, float* G_all, void*
     return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
 }
 
-extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, const float* a_all,
-                              const float* b_all, const ot_options* opt, double* w_all, double* z_all,
-                              ot_result* results, void* workspace, size_t ws_bytes, void* stream) {
-    if (count <= 0 || count > OT_BATCH_MAX || total_m <= 0 || !G_all || !a_all || !b_all || !opt || !w_all ||
-        !z_all || !results || !workspace)
-        return OT_ERR_ARG;
-    if (opt->max_iter < 1 || opt->tol_l1 < 0.0) return OT_ERR_ARG;
-    if (((uintptr_t)G_all) % 16) return OT_ERR_ARG;   // bulk copies of cost rows need 16-byte alignment
-    if (ws_bytes < ot_batch_workspace_bytes(count, total_m) || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
+// ---- launch configurations and the autotuner
+//
+// A configuration code (ot_options.tile_override for the batch solver) packs
+// the pipeline depth, the group-size policy and the convergence-check cadence:
+// 0 is the default (3 stages, tight groups, opt->check_every); otherwise
+// code - 1 = s | (g << 1) | (c << 2) with s = 0 for 3 stages and 1 for 2,
+// g = group-size shift, c = log2 of the check cadence (0..2).
+struct BatchCfg {
+    int stages, gs_shift, check_every;
+};
+
+static bool decode_cfg(int code, int opt_check_every, BatchCfg& c) {
+    if (code == 0) {
+        c.stages = 3;
+        c.gs_shift = 0;
+        c.check_every = opt_check_every >= 1 ? opt_check_every : 1;
+        return true;
+    }
+    code -= 1;
+    if (code < 0 || code >= OT_BATCH_NCFG) return false;
+    c.stages = (code & 1) ? 2 : 3;
+    c.gs_shift = (code >> 1) & 1;
+    c.check_every = 1 << (code >> 2);
+    return true;
+}
+
+static int encode_cfg(const BatchCfg& c) {
+    const int ce = c.check_every >= 4 ? 2 : (c.check_every >= 2 ? 1 : 0);
+    return 1 + ((c.stages == 2) ? 1 : 0) + (c.gs_shift << 1) + (ce << 2);
+}
+
+template <int STAGES>
+static int launch_batch(const BatchArgs& A, cudaStream_t st) {
+    const int sms = device_sms();
+    if (sms <= 0) return OT_ERR_CUDA;
+    const size_t smem = BatchSmem::total;
+    auto kern = batch_solve_kernel<STAGES>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return OT_ERR_CUDA;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, OT_BT, smem) != cudaSuccess || nb < 1)
+        return OT_ERR_UNSUPPORTED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sms);
+    cfg.blockDim = dim3(OT_BT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, A) != cudaSuccess) return OT_ERR_CUDA;
+    return OT_OK;
+}
+
+static int batch_solve_cfg(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
+                           const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
+                           size_t ws_bytes, cudaStream_t st, const BatchCfg& C) {
     char* base = (char*)workspace + a256(sizeof(BatchHeader));
     const BatchLayout L = batch_layout(count, total_m);
     BatchArgs A;
@@ -854,6 +912,8 @@ extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, 
     A.max_iter = opt->max_iter;
     A.timeout_ns = opt->timeout_ns ? opt->timeout_ns : 10000000000ull;
     A.warm = opt->warm_start;
+    A.gs_shift = C.gs_shift;
+    A.check_every = C.check_every;
     A.w_out = w_all;
     A.z_out = z_all;
     A.res = results;
@@ -872,25 +932,150 @@ extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, 
     A.cf = (float*)(base + L.cf);
     A.R = (float*)(base + L.R);
     if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return OT_ERR_CUDA;
-    const int sms = device_sms();
-    if (sms <= 0) return OT_ERR_CUDA;
-    const size_t smem = BatchSmem::total;
-    auto kern = batch_solve_kernel;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return C.stages == 2 ? launch_batch<2>(A, st) : launch_batch<3>(A, st);
+}
+
+static int batch_check_args(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
+                            const ot_options* opt, double* w_all, double* z_all, ot_result* results,
+                            void* workspace, size_t ws_bytes) {
+    if (count <= 0 || count > OT_BATCH_MAX || total_m <= 0 || !G_all || !a_all || !b_all || !opt || !w_all ||
+        !z_all || !results || !workspace)
+        return OT_ERR_ARG;
+    if (opt->max_iter < 1 || opt->tol_l1 < 0.0) return OT_ERR_ARG;
+    if (((uintptr_t)G_all) % 16) return OT_ERR_ARG;   // bulk copies of cost rows need 16-byte alignment
+    if (ws_bytes < ot_batch_workspace_bytes(count, total_m) || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
+    return OT_OK;
+}
+
+extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, const float* a_all,
+                              const float* b_all, const ot_options* opt, double* w_all, double* z_all,
+                              ot_result* results, void* workspace, size_t ws_bytes, void* stream) {
+    const int rc = batch_check_args(count, total_m, G_all, a_all, b_all, opt, w_all, z_all, results, workspace,
+                                    ws_bytes);
+    if (rc != OT_OK) return rc;
+    BatchCfg C;
+    if (!decode_cfg(opt->tile_override, opt->check_every, C)) return OT_ERR_ARG;
+    return batch_solve_cfg(count, total_m, G_all, a_all, b_all, opt, w_all, z_all, results, workspace, ws_bytes,
+                           (cudaStream_t)stream, C);
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, unsigned long long>, int> g_tune_cache;   // (device, batch signature) -> code
+
+// FNV-1a over the problem table and the stopping parameters.
+unsigned long long batch_signature(const ot_problem_desc* d, int count, const ot_options* opt) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* c = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    };
+    for (int i = 0; i < count; ++i) {
+        mix(&d[i].m, sizeof(int));
+        mix(&d[i].N, sizeof(int));
+        mix(&d[i].eps, sizeof(float));
+        mix(&d[i].ld, sizeof(int));
+    }
+    mix(&opt->tol_l1, sizeof(double));
+    mix(&opt->max_iter, sizeof(int));
+    return h;
+}
+}  // namespace
+
+extern "C" int ot_batch_autotune(int count, long long total_m, const float* G_all, const float* a_all,
+                                 const float* b_all, const ot_options* opt, double* w_all, double* z_all,
+                                 ot_result* results, void* workspace, size_t ws_bytes, void* stream,
+                                 int* config_out, float* ms_out) {
+    int rc = batch_check_args(count, total_m, G_all, a_all, b_all, opt, w_all, z_all, results, workspace, ws_bytes);
+    if (rc != OT_OK) return rc;
+    if (!config_out) return OT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return OT_ERR_ARG;
+    // signature of the prepared problem table
+    std::vector<ot_problem_desc> h(count);
+    const BatchLayout L = batch_layout(count, total_m);
+    const char* base = (const char*)workspace + a256(sizeof(BatchHeader));
+    if (cudaMemcpyAsync(h.data(), base + L.desc, sizeof(ot_problem_desc) * (size_t)count, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return OT_ERR_CUDA;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, OT_BT, smem) != cudaSuccess || nb < 1)
-        return OT_ERR_UNSUPPORTED;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(sms);
-    cfg.blockDim = dim3(OT_BT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, kern, A) != cudaSuccess) return OT_ERR_CUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return OT_ERR_CUDA;
+    const auto key = std::make_pair(dev, batch_signature(h.data(), count, opt));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *config_out = it->second;
+            return OT_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OT_ERR_CUDA;
+    auto timed = [&](const BatchCfg& C, const ot_options& o, float& ms) -> int {
+        float best = 3.4e38f;
+        for (int rep = 0; rep < 2; ++rep) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return OT_ERR_CUDA;
+            int r = batch_solve_cfg(count, total_m, G_all, a_all, b_all, &o, w_all, z_all, results, workspace,
+                                    ws_bytes, st, C);
+            if (r != OT_OK) return r;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return OT_ERR_CUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = t < best ? t : best;
+        }
+        ms = best;
+        return OT_OK;
+    };
+    // 1. pipeline depth and group-size policy: a few full sweeps (no problem stops early)
+    ot_options o = *opt;
+    o.warm_start = 0;
+    o.tol_l1 = 0.0;
+    o.max_iter = 4;
+    BatchCfg best;
+    best.stages = 3;
+    best.gs_shift = 0;
+    best.check_every = 1;
+    float best_ms = 3.4e38f;
+    for (int code = 1; code <= 4 && rc == OT_OK; ++code) {
+        BatchCfg C;
+        decode_cfg(code, 1, C);
+        float ms = 0.f;
+        rc = timed(C, o, ms);
+        if (ms_out) ms_out[code - 1] = ms;
+        if (rc == OT_OK && ms < best_ms) {
+            best_ms = ms;
+            best = C;
+        }
+    }
+    // 2. convergence-check cadence: complete solves with the caller's stopping rule
+    o = *opt;
+    o.warm_start = 0;
+    float best_full = 3.4e38f;
+    int best_ce = 1;
+    for (int ce = 1; ce <= 4 && rc == OT_OK; ce <<= 1) {
+        BatchCfg C = best;
+        C.check_every = ce;
+        float ms = 0.f;
+        rc = timed(C, o, ms);
+        if (ms_out) ms_out[4 + (ce == 1 ? 0 : (ce == 2 ? 1 : 2))] = ms;
+        if (rc == OT_OK && ms < best_full) {
+            best_full = ms;
+            best_ce = ce;
+        }
+    }
+    best.check_every = best_ce;
+    // leave the outputs of a complete solve with the chosen configuration
+    if (rc == OT_OK)
+        rc = batch_solve_cfg(count, total_m, G_all, a_all, b_all, &o, w_all, z_all, results, workspace, ws_bytes, st,
+                             best);
+    if (rc == OT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = OT_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != OT_OK) return rc;
+    *config_out = encode_cfg(best);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = *config_out;
     return OT_OK;
 }

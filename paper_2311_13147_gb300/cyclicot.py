@@ -337,6 +337,10 @@ def _batch_lib():
         L.ot_batch_solve.restype = ctypes.c_int
         L.ot_batch_solve.argtypes = [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.POINTER(ot_options),
                                      _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.ot_batch_autotune.restype = ctypes.c_int
+        L.ot_batch_autotune.argtypes = [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.POINTER(ot_options),
+                                        _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_float)]
         L._batch_ready = True
     return L
 
@@ -372,3 +376,15 @@ def read_results(res: torch.Tensor, count: int):
         r = ot_result.from_buffer_copy(raw[64 * p:64 * (p + 1)])
         out.append({"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1})
     return out
+
+
+def ot_batch_autotune(count: int, total_m: int, G_all, a_all, b_all, opt: ot_options, w_all, z_all, results,
+                      workspace_t, stream=None):
+    """Returns (configuration code, measured candidate times in ms)."""
+    code = ctypes.c_int(0)
+    ms = (ctypes.c_float * 7)()
+    rc = _batch_lib().ot_batch_autotune(int(count), int(total_m), _ptr(G_all), _ptr(a_all), _ptr(b_all),
+                                        ctypes.byref(opt), _ptr(w_all), _ptr(z_all), _ptr(results),
+                                        _ptr(workspace_t), workspace_t.numel(), _stream(stream), ctypes.byref(code), ms)
+    _check(rc, "ot_batch_autotune")
+    return code.value, list(ms)

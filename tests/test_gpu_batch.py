@@ -137,3 +137,46 @@ def test_batch_argument_errors(cy):
         cy.ot_batch_prepare(d, small)
     assert cy.ot_batch_workspace_bytes(0, 8) == 0
     assert cy.ot_batch_workspace_bytes(2000, 8) == 0
+
+
+def test_batch_autotune_and_configurations(cy):
+    """Every launch configuration solves the batch; the tuner returns a valid, cached code."""
+    from paper_2311_13147_gb300.batch import BatchSolver
+    probs, costs = zip(*[f32_problem(*c) for c in CASES[:6]])
+    tol = 1e-6
+    bs = BatchSolver(list(probs), tol=tol)
+    iters = {}
+    for code in range(1, 13):
+        bs.opt.tile_override = code
+        bs.w.zero_()
+        bs.z.zero_()
+        bs.run()
+        torch.cuda.synchronize()
+        res = bs.results()
+        cadence = 1 << ((code - 1) >> 2)
+        for idx, r in enumerate(res):
+            assert r["status"] == cy.OT_OK, (code, idx, r)
+            assert r["marg_l1"] <= tol
+            assert r["iters"] % cadence == 0
+        iters[code] = [r["iters"] for r in res]
+        w, z = (t.cpu().numpy() for t in bs.potentials(3))
+        p, C = probs[3], costs[3]
+        rl1, cl1 = oracle_marginal_errors(w, z, C, p.a_base, p.b_base, p.eps)
+        assert rl1 <= tol + 1e-6 and cl1 <= 1e-6, (code, rl1, cl1)
+    # the cadence only delays the stop to the next multiple (up to a rounding flip at the threshold)
+    for code in range(1, 13):
+        base = iters[1 + ((code - 1) & 3)]
+        cadence = 1 << ((code - 1) >> 2)
+        for a, b in zip(iters[code], base):
+            assert b - 1 <= a <= b + cadence, (code, a, b)
+    bs.opt.tile_override = 0
+    code = bs.autotune()
+    assert 1 <= code <= 12
+    res = bs.results()
+    assert all(r["status"] == cy.OT_OK for r in res)
+    code2, _ = cy.ot_batch_autotune(bs.count, bs.total_m, bs.G, bs.a, bs.b, bs.opt, bs.w, bs.z, bs.res, bs.ws)
+    assert code2 == code
+    bad = cy.options(1.0, tol=tol)
+    bad.tile_override = 13
+    with pytest.raises(cy.OTError):
+        cy.ot_batch_solve(bs.count, bs.total_m, bs.G, bs.a, bs.b, bad, bs.w, bs.z, bs.res, bs.ws)
