@@ -13,6 +13,12 @@ block-circulant plan, value + marginal norms + envelope gradient.  The plain
 full-size Sinkhorn on the stored n x n cost is timed beside it on the same
 inputs (``full`` key).  L2 is flushed (a 512 MB write) before every timed step.
 
+``--workload batch``: 512 independent ring-cloud problems, n ~ U[1024, 16384],
+N ~ U{2, 3, 4, 6, 8}, Dirichlet(0.5) marginals, eps = 0.01 * max C, folded
+from the point coordinates and solved to 1e-6 in one persistent launch each
+(fold + solve replayed as a CUDA graph, launch configuration autotuned first).
+The 17.7 GB of folded costs exceed L2, so no flush is needed.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle
 on a bounded sample of the same workload instead.
 """
@@ -41,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="image_grid", choices=["image_grid"])
+    ap.add_argument("--workload", default="image_grid", choices=["image_grid", "batch"])
     ap.add_argument("--eps-frac", type=float, default=0.01)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -341,6 +347,185 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- batch workload
+
+def batch_workload(args):
+    from paper_2311_13147_gb300 import inputs as I
+    probs = I.batch_problems(count=512, seed=0, eps_frac=args.eps_frac)
+    ms = [p.m for p in probs]
+    cfg = {"workload": "batch_512_ring_N2-8_n1024-16384", "count": len(probs), "m_min": min(ms), "m_max": max(ms),
+           "sum_m2": int(sum(m * m for m in ms)), "eps_frac_of_max_cost": args.eps_frac, "tol_l1": args.tol,
+           "cost": "folded on the GPU from point coordinates (fp32)",
+           "l2": "not flushed: the 17.7 GB of folded costs exceed the 129 MB L2"}
+    return probs, cfg
+
+
+def run_ours_batch(args, rank, world, local_rank):
+    import torch
+    from paper_2311_13147_gb300 import build as B
+    from paper_2311_13147_gb300 import cyclicot as cy
+    from paper_2311_13147_gb300.batch import BatchSolver
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    probs, cfg = batch_workload(args)
+    bs = BatchSolver(probs, tol=args.tol, max_iter=100000, device=f"cuda:{local_rank}")
+    bs.fold()
+    code = bs.autotune()
+    tuning_ms = bs.tuning_ms
+    bs.capture()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bs.replay()
+    torch.cuda.synchronize()
+    res = bs.results()
+    if any(r["status"] != cy.OT_OK for r in res):
+        raise RuntimeError("batch solve failed: " + str([r for r in res if r["status"] != cy.OT_OK][:3]))
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bs.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=f"cuda:{local_rank}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt[0])
+    res = bs.results()
+    iters = np.array([r["iters"] for r in res])
+    # solver kernel alone (eager launch of the same configuration) for the roofline
+    solve_ms = []
+    for _ in range(3):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        bs.solve()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        solve_ms.append(a0.elapsed_time(a1))
+    solve_ms = float(np.median(solve_ms))
+    # algorithmic bytes: one FP32 read of each active problem's folded cost per sweep
+    # (iters + 1 sweeps: the last one measures the returned state)
+    alg_bytes = float(sum(4.0 * d.m * d.ld * (r["iters"] + 1) for d, r in zip(bs.descs, res)))
+    achieved = alg_bytes / (solve_ms / 1e3) / 1e9
+    peaks, peak_src = load_peaks()
+    traffic = profile_traffic("batch_solve_kernel.batch512.md", "batch.cu")
+    # e2e through the public API: host inputs (pinned) in, potentials and results out, every step
+    h_pts = bs.points.cpu().pin_memory()
+    h_a = bs.a.cpu().pin_memory()
+    h_b = bs.b.cpu().pin_memory()
+    h_w = torch.empty_like(bs.w, device="cpu").pin_memory()
+    h_z = torch.empty_like(bs.z, device="cpu").pin_memory()
+    h_r = torch.empty_like(bs.res, device="cpu").pin_memory()
+
+    def e2e_step():
+        bs.points.copy_(h_pts, non_blocking=True)
+        bs.a.copy_(h_a, non_blocking=True)
+        bs.b.copy_(h_b, non_blocking=True)
+        bs.replay()
+        h_w.copy_(bs.w, non_blocking=True)
+        h_z.copy_(bs.z, non_blocking=True)
+        h_r.copy_(bs.res, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = f0.elapsed_time(f1)
+    h2d = (h_pts.numel() + h_a.numel() + h_b.numel()) * 4
+    d2h = (h_w.numel() + h_z.numel()) * 8 + h_r.numel()
+    count = bs.count
+    out = {
+        "metric": METRIC, "value": world * count * args.steps / (t_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": dict(cfg, parallelism="replicas" if world > 1 else "single", launch_config=code),
+        "iters": {"min": int(iters.min()), "median": float(np.median(iters)), "max": int(iters.max()),
+                  "sum": int(iters.sum())},
+        "autotune_ms": tuning_ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "kernel": "batch_solve_kernel (one FP32 read of every active problem's folded cost per sweep)",
+                     "solve_ms": solve_ms, "alg_bytes": alg_bytes},
+        "e2e": {"value": world * count * args.steps / (t_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "kernels_per_step": ["batch_fold_kernel", "batch_solve_kernel"],
+        "clocks": clk,
+    }
+    return out, (probs, iters)
+
+
+def cpu_oracle_batch(args, probs, iters, budget_s):
+    """Oracle on a bounded sample: fold + 3 iterations on a few problems, per-iteration cost fitted
+    as c * m^2 and extrapolated over the batch with the GPU's iteration counts."""
+    from paper_2311_13147_gb300 import inputs as I
+    from oracle import sinkhorn as OS
+    order = np.argsort([p.m for p in probs])
+    pick = [order[0], order[len(order) // 4], order[len(order) // 2]]
+    t_fold, t_it, used = [], [], []
+    t_start = time.perf_counter()
+    for i in pick:
+        p = probs[i]
+        C = I.cost_blocks_from_points(np.asarray(p.x, np.float64), np.asarray(p.y, np.float64), p.N)
+        t0 = time.perf_counter()
+        OS.fold_softmin(C, p.eps)
+        t1 = time.perf_counter()
+        OS.cyclic_sinkhorn(p.a_base, p.b_base, C, p.eps, tol=0.0, max_iter=3)
+        t2 = time.perf_counter()
+        t_fold.append((t1 - t0) / (p.N * p.m * p.m))
+        t_it.append(max(t2 - t1 - (t1 - t0), 1e-9) / (3 * p.m * p.m))
+        used.append(p.m)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    cf, ci = float(np.median(t_fold)), float(np.median(t_it))
+    total = sum(cf * p.N * p.m * p.m + ci * p.m * p.m * (k + 1) for p, k in zip(probs, iters))
+    return total, used
+
+
+def run_reference_batch(args, rank, world):
+    from oracle import sinkhorn as OS
+    from paper_2311_13147_gb300 import inputs as I
+    probs, cfg = batch_workload(args)
+    # iteration counts: the oracle's own, run to the tolerance on the three smallest problems;
+    # their median stands in for every problem of the batch
+    small = np.argsort([p.m for p in probs])[:3]
+    its = []
+    for i in small:
+        p = probs[i]
+        C = I.cost_blocks_from_points(np.asarray(p.x, np.float64), np.asarray(p.y, np.float64), p.N)
+        its.append(OS.cyclic_sinkhorn(p.a_base, p.b_base, C, p.eps, tol=args.tol, max_iter=100000)["iters"])
+    iters = np.full(len(probs), int(np.median(its)))
+    times = []
+    used = []
+    budget = max(2.0, args.cpu_budget_s / max(1, args.steps + args.warmup))
+    for s_ in range(args.warmup + args.steps):
+        t, used = cpu_oracle_batch(args, probs, iters, budget)
+        if s_ >= args.warmup:
+            times.append(t)
+    t = float(np.mean(times))
+    value = len(probs) / t
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"fold + 3 iterations on problems with m = {used}, per-entry costs "
+                                       f"extrapolated over the 512 problems at {int(iters[0])} iterations each "
+                                       f"(the oracle's median count to {args.tol:g} on the three smallest)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -349,12 +534,30 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        print(json.dumps(run_reference(args, rank, world)))
+        if args.workload == "batch":
+            print(json.dumps(run_reference_batch(args, rank, world)))
+        else:
+            print(json.dumps(run_reference(args, rank, world)))
         return
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.workload == "batch":
+        out, (probs, iters) = run_ours_batch(args, rank, world, local_rank)
+        if rank == 0 and not args.no_cpu_baseline:
+            t, used = cpu_oracle_batch(args, probs, iters, args.cpu_budget_s)
+            out["cpu_baseline"] = {"value": len(probs) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"numpy FP64 fold + 3 cyclic Sinkhorn iterations on problems with "
+                                             f"m = {used}; per-entry costs extrapolated over the batch with the "
+                                             f"solver's iteration counts"}
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        if rank == 0:
+            print(json.dumps(out))
+        return
     out, p = run_ours(args, rank, world, local_rank)
     if rank == 0 and not args.no_cpu_baseline:
         t_fold, t_iter, k = cpu_oracle_time(args, p, args.cpu_budget_s)
