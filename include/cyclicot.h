@@ -328,6 +328,45 @@ int ot_batch_autotune(int count, long long total_m, const float* G_all, const fl
                       const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
                       size_t ws_bytes, void* stream, int* config_out, float* ms_out);
 
+/* ---- form 1: BF16 kernel-domain iterations on the tensor cores ----------- */
+
+/* Workspace bytes of ot_kdomain_solve for block size m (0 if m is out of range). */
+size_t ot_kdomain_workspace_bytes(int m);
+
+/*
+ * ot_kdomain_solve -- Algorithm 2 in scaling form (Eq.
+ * optimal_f_sinkhorn_logdomain exponentiated: U = alpha ./ (K V),
+ * V = beta ./ (K^T U), K = exp(-G / eps)) for nrhs <= 64 histogram pairs that
+ * share one folded cost G.  K, K^T and the scalings are BF16 operands of
+ * tcgen05 tensor-core products with FP32 accumulation; the scalings are kept
+ * in FP32 between products.  Runs exactly `iters` iterations from V = 1 (no
+ * stopping rule: BF16 bounds the reachable accuracy near 1e-3; polish the
+ * result with ot_batch_solve, warm-started from z).
+ *  G: [m][ld] FP32 device, ld >= m.  a_hist, b_hist: [nrhs][m] FP32 device,
+ *     positive entries (each pair is normalised to unit mass).
+ *  z_out: [nrhs][m] FP64 device, eps ln V (the column potential of the
+ *     unit-mass reduced problem; a zero scaling maps to eps ln 1e-37).
+ *  row_err: NULL or [iters][64] FP32 device: entry [t][n] is the L1 row
+ *     marginal error of pair n before iteration t's row update (the state after
+ *     t column updates).
+ *  m <= 16384 (padded internally to a multiple of 128).  Asynchronous; a
+ *  device wait that expires is reported by ot_kdomain_status.
+ */
+int ot_kdomain_solve(int m, const float* G, int ld, float eps, int nrhs, const float* a_hist, const float* b_hist,
+                     int iters, double* z_out, float* row_err, void* workspace, size_t ws_bytes, void* stream);
+
+/* Error flag of the last ot_kdomain_solve on `workspace` (blocks on stream). */
+int ot_kdomain_status(const void* workspace, int m, int* status, void* stream);
+
+/*
+ * ot_kdomain_product -- the tensor-core product used by ot_kdomain_solve:
+ * Dt[n][i] = sum_k A[i][k] X[n][k] for n < 64, i < mp; A [mp][mp] BF16,
+ * X [64][mp] BF16, Dt [64][mp] FP32 (device, 16-byte aligned; mp a multiple
+ * of 128, <= 16384).  Blocks until done; returns OT_ERR_TIMEOUT if a device
+ * wait expired.
+ */
+int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,3 +95,56 @@ class BatchSolver:
     def cost(self, p):
         d = self.descs[p]
         return self.G[d.g_off:d.g_off + d.m * d.ld].view(d.m, d.ld)[:, :d.m]
+
+
+class SharedCostBatch:
+    """Up to 64 histogram pairs on one cyclic cost: BF16 kernel-domain iterations on the
+    tensor cores, then the FP32 log-domain batch solver warm-started from their potentials.
+
+    points: base source / target coordinates [m][2] (cost |x_i - R^k y_j|^2);
+    a_hist, b_hist: [P][m] marginals (P <= 64).
+    """
+
+    def __init__(self, x, y, N, eps, a_hist, b_hist, tol=1e-6, max_iter=20000, device="cuda"):
+        dev = torch.device(device)
+        x = np.asarray(x, np.float32)
+        y = np.asarray(y, np.float32)
+        self.m = m = x.shape[0]
+        self.N, self.eps = int(N), float(eps)
+        self.P = P = a_hist.shape[0]
+        self.ld = ld = (m + 3) // 4 * 4
+        self.descs = [cy.ot_problem_desc(m, self.N, self.eps, ld, 0, p * m, 0, m) for p in range(P)]
+        self.points = torch.from_numpy(np.concatenate([x, y])).to(dev)
+        self.a = torch.from_numpy(np.ascontiguousarray(a_hist, np.float32)).to(dev)
+        self.b = torch.from_numpy(np.ascontiguousarray(b_hist, np.float32)).to(dev)
+        self.G = torch.empty(m * ld, dtype=torch.float32, device=dev)
+        self.w = torch.zeros(P * m, dtype=torch.float64, device=dev)
+        self.z = torch.zeros(P * m, dtype=torch.float64, device=dev)
+        self.res = torch.zeros(64 * P, dtype=torch.uint8, device=dev)
+        self.ws = torch.empty(cy.ot_batch_workspace_bytes(P, P * m), dtype=torch.uint8, device=dev)
+        self.kws = torch.empty(cy.ot_kdomain_workspace_bytes(m), dtype=torch.uint8, device=dev)
+        self.opt = cy.options(1.0, tol=tol, max_iter=max_iter)
+        cy.ot_batch_prepare(self.descs, self.ws)
+
+    def fold(self):
+        cy.ot_batch_fold(1, self.points, self.G, self.ws)   # one shared cost
+
+    def kernel_domain(self, iters, row_err=None):
+        """BF16 tensor-core iterations; leaves z = eps ln V in self.z."""
+        cy.ot_kdomain_solve(self.m, self.G, self.ld, self.eps, self.a, self.b, iters,
+                            z_out=self.z.view(self.P, self.m), row_err=row_err, workspace_t=self.kws)
+
+    def polish(self, warm=True):
+        self.opt.warm_start = 1 if warm else 0
+        cy.ot_batch_solve(self.P, self.P * self.m, self.G, self.a.view(-1), self.b.view(-1), self.opt,
+                          self.w, self.z, self.res, self.ws)
+
+    def results(self):
+        return cy.read_results(self.res, self.P)
+
+    def potentials(self, p):
+        m = self.m
+        return self.w[p * m:(p + 1) * m], self.z[p * m:(p + 1) * m]
+
+    def cost(self):
+        return self.G.view(self.m, self.ld)[:, :self.m]

@@ -388,3 +388,51 @@ def ot_batch_autotune(count: int, total_m: int, G_all, a_all, b_all, opt: ot_opt
                                         _ptr(workspace_t), workspace_t.numel(), _stream(stream), ctypes.byref(code), ms)
     _check(rc, "ot_batch_autotune")
     return code.value, list(ms)
+
+
+# ------------------------------------------------------------------ kernel domain (BF16, tensor cores)
+
+def _kd_lib():
+    L = lib()
+    if not getattr(L, "_kd_ready", False):
+        L.ot_kdomain_workspace_bytes.restype = ctypes.c_size_t
+        L.ot_kdomain_workspace_bytes.argtypes = [ctypes.c_int]
+        L.ot_kdomain_solve.restype = ctypes.c_int
+        L.ot_kdomain_solve.argtypes = [ctypes.c_int, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int, _vp, _vp,
+                                       ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.ot_kdomain_status.restype = ctypes.c_int
+        L.ot_kdomain_status.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
+        L.ot_kdomain_product.restype = ctypes.c_int
+        L.ot_kdomain_product.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp]
+        L._kd_ready = True
+    return L
+
+
+def ot_kdomain_workspace_bytes(m: int) -> int:
+    return int(_kd_lib().ot_kdomain_workspace_bytes(int(m)))
+
+
+def ot_kdomain_solve(m: int, G, ld: int, eps: float, a_hist, b_hist, iters: int, z_out=None, row_err=None,
+                     workspace_t=None, stream=None):
+    nrhs = a_hist.shape[0]
+    dev = G.device
+    if z_out is None:
+        z_out = torch.empty((nrhs, m), dtype=torch.float64, device=dev)
+    if workspace_t is None:
+        workspace_t = torch.empty(ot_kdomain_workspace_bytes(m), dtype=torch.uint8, device=dev)
+    rc = _kd_lib().ot_kdomain_solve(int(m), _ptr(G), int(ld), float(eps), int(nrhs), _ptr(a_hist), _ptr(b_hist),
+                                    int(iters), _ptr(z_out), _ptr(row_err) if row_err is not None else None,
+                                    _ptr(workspace_t), workspace_t.numel(), _stream(stream))
+    _check(rc, "ot_kdomain_solve")
+    return z_out, workspace_t
+
+
+def ot_kdomain_status(workspace_t, m: int, stream=None) -> int:
+    st = ctypes.c_int(0)
+    _check(_kd_lib().ot_kdomain_status(_ptr(workspace_t), int(m), ctypes.byref(st), _stream(stream)),
+           "ot_kdomain_status")
+    return st.value
+
+
+def ot_kdomain_product(mp: int, A, X, Dt, stream=None):
+    _check(_kd_lib().ot_kdomain_product(int(mp), _ptr(A), _ptr(X), _ptr(Dt), _stream(stream)), "ot_kdomain_product")

@@ -315,6 +315,18 @@ def batch_problems(count: int = 512, seed: int = 0, n_lo: int = 1024, n_hi: int 
     return out
 
 
+def histogram_pairs(m: int, count: int = 64, seed: int = 0, dirichlet: float = 0.5):
+    """`count` (a_base, b_base) pairs ~ Dirichlet(dirichlet * 1_m), clamped and normalised, float32 [count][m].
+
+    The "64 shared-cost histograms per cost" of the precision workload: every
+    pair is a separate transport problem on the same folded cost.
+    """
+    rng = np.random.default_rng(seed)
+    a = np.stack([_normalise(rng.dirichlet(dirichlet * np.ones(m))) for _ in range(count)])
+    b = np.stack([_normalise(rng.dirichlet(dirichlet * np.ones(m))) for _ in range(count)])
+    return a.astype(np.float32), b.astype(np.float32)
+
+
 def bench_sizes():
     """Named workload sizes (block size m, order N) used by the benchmark."""
     return {
