@@ -19,6 +19,11 @@ from the point coordinates and solved to 1e-6 in one persistent launch each
 (fold + solve replayed as a CUDA graph, launch configuration autotuned first).
 The 17.7 GB of folded costs exceed L2, so no flush is needed.
 
+``--workload precision``: 8 costs of that batch (m from 158 to 8162), each
+carrying 64 Dirichlet(0.5) histogram pairs; FP32 log-domain solves of all 64
+pairs against BF16 kernel-domain tensor-core iterations plus the FP32 polish,
+both to 1e-6, with objective errors against the FP64 oracle on a sample.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle
 on a bounded sample of the same workload instead.
 """
@@ -47,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="image_grid", choices=["image_grid", "batch"])
+    ap.add_argument("--workload", default="image_grid", choices=["image_grid", "batch", "precision"])
     ap.add_argument("--eps-frac", type=float, default=0.01)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -526,6 +531,137 @@ def run_reference_batch(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- precision workload (form 1)
+
+PRECISION_BF16_ITERS = 60
+
+
+def precision_workload(args):
+    from paper_2311_13147_gb300 import inputs as I
+    probs = I.batch_problems(count=512, seed=0, eps_frac=args.eps_frac)
+    order = np.argsort([p.m for p in probs])
+    pick = [int(order[int(round(q * (len(order) - 1)))]) for q in np.linspace(0.0, 1.0, 8)]
+    costs = [probs[i] for i in pick]
+    hist = [I.histogram_pairs(p.m, 64, seed=1000 + i) for i, p in zip(pick, costs)]
+    cfg = {"workload": "precision_8costs_x64pairs", "costs": len(costs), "pairs_per_cost": 64,
+           "m": [p.m for p in costs], "N": [p.N for p in costs], "eps_frac_of_max_cost": args.eps_frac,
+           "tol_l1": args.tol, "bf16_iters": PRECISION_BF16_ITERS,
+           "l2": "not flushed; the costs are re-folded inside every step"}
+    return costs, hist, cfg
+
+
+def run_ours_precision(args, rank, world, local_rank):
+    import torch
+    from paper_2311_13147_gb300 import build as B
+    from paper_2311_13147_gb300 import cyclicot as cy
+    from paper_2311_13147_gb300.batch import SharedCostBatch
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    costs, hist, cfg = precision_workload(args)
+    sbs = [SharedCostBatch(p.x, p.y, p.N, p.eps, a, b, tol=args.tol, max_iter=20000)
+           for p, (a, b) in zip(costs, hist)]
+    stream = torch.cuda.current_stream()
+
+    def fp32_step():
+        for sb in sbs:
+            sb.fold()
+            sb.z.zero_()
+            sb.polish(warm=False)
+
+    def bf16_step():
+        for sb in sbs:
+            sb.fold()
+            sb.kernel_domain(PRECISION_BF16_ITERS)
+            sb.polish(warm=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t32 = timed(fp32_step)
+    it32 = [sum(r["iters"] for r in sb.results()) for sb in sbs]
+    ok32 = all(r["status"] == cy.OT_OK for sb in sbs for r in sb.results())
+    t16 = timed(bf16_step)
+    it16 = [sum(r["iters"] for r in sb.results()) for sb in sbs]
+    ok16 = all(r["status"] == cy.OT_OK for sb in sbs for r in sb.results())
+    clk = clocks.stop()
+    if not (ok32 and ok16):
+        raise RuntimeError("precision workload: a solve did not converge")
+    # BF16 stage alone on the largest cost, for the tensor-core roofline
+    sb = sbs[-1]
+    mp = (sb.m + 127) // 128 * 128
+    ts = {}
+    for k in (10, 30):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sb.kernel_domain(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts[k] = e0.elapsed_time(e1)
+    per_iter_ms = (ts[30] - ts[10]) / 20
+    flops = 2 * 2.0 * mp * mp * 64      # two [mp x mp] x [mp x 64] products per iteration
+    kbytes = 2 * 2.0 * mp * mp          # the BF16 K and K^T read once each
+    peaks, peak_src = load_peaks()
+    tflops = flops / (per_iter_ms / 1e3) / 1e12
+    gbs = kbytes / (per_iter_ms / 1e3) / 1e9
+    pairs = 64 * len(sbs)
+    out = {
+        "metric": METRIC, "value": pairs / (t16 / 1e3), "unit": "pair solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t16, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (seeded)",
+        "config": dict(cfg, parallelism="single"),
+        "fp32_log_domain": {"ms_per_step": t32, "pair_solves_per_s": pairs / (t32 / 1e3), "iters_per_cost": it32},
+        "bf16_then_polish": {"ms_per_step": t16, "polish_iters_per_cost": it16},
+        "speedup_bf16_vs_fp32": t32 / t16,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": f"kd_gemm_kernel pair per BF16 iteration at mp = {mp} (K and K^T read once)",
+                     "tensor_tflops": tflops,
+                     "tensor_frac_of_bf16_peak": tflops / peaks.get("bf16_tflops", 1900.0),
+                     "ms_per_bf16_iter": per_iter_ms},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    # objective errors against the FP64 oracle on the two smallest costs (4 pairs each)
+    from oracle import sinkhorn as OS
+    from paper_2311_13147_gb300 import inputs as I
+    errs = []
+    for sb, p, (a, b) in list(zip(sbs, costs, hist))[:2]:
+        C = I.cost_blocks_from_points(np.asarray(p.x, np.float32).astype(np.float64),
+                                      np.asarray(p.y, np.float32).astype(np.float64), p.N)
+        sb.fold()
+        sb.kernel_domain(PRECISION_BF16_ITERS)
+        torch.cuda.synchronize()
+        zb = sb.z.cpu().numpy().reshape(sb.P, sb.m)
+        sb.polish(warm=True)
+        torch.cuda.synchronize()
+        for q in range(4):
+            ref = OS.cyclic_sinkhorn(a[q], b[q], C, p.eps, tol=1e-12)
+            v_ref = OS.primal_value_reduced(OS.unfold_erot(ref["w"], ref["z"], C, p.eps), C, p.eps)["value"]
+            w, z = (t.cpu().numpy() for t in sb.potentials(q))
+            v_pol = OS.primal_value_reduced(OS.unfold_erot(w, z, C, p.eps), C, p.eps)["value"]
+            # BF16 stage: its column potential with the matching row update
+            G = OS.fold_softmin(C, p.eps)
+            alpha, _ = OS.base_marginals(a[q], b[q], p.N)
+            wb = p.eps * np.log(alpha) - p.eps * OS.lse((zb[q][None, :] - G) / p.eps, axis=1)
+            v_b = OS.primal_value_reduced(OS.unfold_erot(wb, zb[q], C, p.eps), C, p.eps)["value"]
+            errs.append({"m": p.m, "pair": q, "rel_err_bf16_stage": abs(v_b - v_ref) / abs(v_ref),
+                         "rel_err_after_polish": abs(v_pol - v_ref) / abs(v_ref)})
+    out["objective_errors_vs_fp64"] = errs
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -543,6 +679,11 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.workload == "precision":
+        out = run_ours_precision(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.workload == "batch":
         out, (probs, iters) = run_ours_batch(args, rank, world, local_rank)
         if rank == 0 and not args.no_cpu_baseline:

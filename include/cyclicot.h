@@ -295,9 +295,9 @@ int ot_batch_fold(int count, const float* points, float* G_all, void* workspace,
  * convention, as ot_sinkhorn_reduced) at v_off, and results[p] (device array
  * of `count` ot_result: iters, status, marg_l1).  total_m = max over problems
  * of v_off + m (the length of the vector buffers), as given to prepare.
- * opt->tile_override selects a launch configuration: 0 = default (3-stage
- * pipeline, tight thread groups, convergence tested every opt->check_every
- * iterations), or a code returned by ot_batch_autotune (1..12).  With a
+ * opt->tile_override selects a launch configuration: 0 = default (tight
+ * thread groups, convergence tested every opt->check_every iterations), or a
+ * code returned by ot_batch_autotune (1..6).  With a
  * cadence k > 1 a problem stops at the first multiple of k whose state meets
  * the tolerance.
  * G_all must be 16-byte aligned (cost rows are streamed with bulk copies);
@@ -313,11 +313,12 @@ int ot_batch_solve(int count, long long total_m, const float* G_all, const float
 /*
  * ot_batch_autotune -- choose the batch solver's launch configuration for a
  * prepared batch on the current device (no counterpart in the paper: an
- * implementation choice).  Times, on `stream`, the pipeline depth x group-size
- * policy candidates over 4 full sweeps, then the convergence-check cadences
- * 1, 2, 4 with complete solves under opt's tolerance; returns the fastest code
- * in *config_out (pass it as ot_options.tile_override to ot_batch_solve).
- * ms_out (host, 7 floats, may be NULL) receives the measured times.  The
+ * implementation choice).  Times, on `stream`, the two group-size policies
+ * (the smallest thread group covering a row, or one size larger) over 4 full
+ * sweeps, then the convergence-check cadences 1, 2, 4 with complete solves
+ * under opt's tolerance; returns the fastest code in *config_out (pass it as
+ * ot_options.tile_override to ot_batch_solve).  ms_out (host, 5 floats, may
+ * be NULL) receives the measured times.  The
  * result is cached per (device, problem table, tol, max_iter): a repeated call
  * returns the cached code without launching anything.  Otherwise the outputs
  * (w, z, results) are those of a complete solve with the chosen code.  Blocks

@@ -42,8 +42,8 @@ int device_sms();
 #define OT_BT 512             // threads per block
 #define OT_BW (OT_BT / 32)
 #define OT_BV 4               // float4 column slots per thread and row
-#define OT_STAGES_MAX 3       // chunks in flight per block (bulk copies into shared memory)
-#define OT_BATCH_NCFG 12      // tunable launch configurations (see decode_cfg)
+#define OT_STAGES_MAX 2       // chunks in flight per block (bulk copies into shared memory)
+#define OT_BATCH_NCFG 6       // tunable launch configurations (see decode_cfg)
 
 struct BatchArgs {
     int count;
@@ -77,12 +77,15 @@ struct BatchArgs {
     float* R;                      // [total_m] column sums
 };
 
-// Dynamic shared memory of the solver: up to OT_STAGES_MAX chunk stages (two rows per
-// group) filled by bulk copies, prefix sums, block sizes and active flags.
+// Dynamic shared memory of the solver: OT_STAGES_MAX chunk stages (two rows per
+// group) filled by bulk copies, the current problem's staged column data,
+// prefix sums, block sizes and active flags.
 constexpr size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 struct BatchSmem {
     static constexpr size_t stage = 0;
-    static constexpr size_t pref = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES_MAX);
+    static constexpr size_t gc = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES_MAX);
+    static constexpr size_t cf = a128(gc + sizeof(float) * OT_BATCH_MAXM);
+    static constexpr size_t pref = a128(cf + sizeof(float) * OT_BATCH_MAXM);
     static constexpr size_t msz = a128(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
     static constexpr size_t act = a128(msz + sizeof(int) * OT_BATCH_MAX);
     static constexpr size_t total = a128(act + sizeof(int) * OT_BATCH_MAX);
@@ -216,11 +219,11 @@ __device__ __forceinline__ void load_scalars(RowScalars& R, const BatchArgs& A, 
     R.rf = X.t > 1 ? A.frf[X.cur * X.TM + gi] : 1.f;
 }
 
-// The column data a thread owns for a whole segment: hi parts of the column
-// potentials and their lo factors (padding: -inf and 0).
-struct ColRegs {
-    float4 gc[OT_BV];
-    float4 cf[OT_BV];
+// The staged column data of the current problem (shared memory): hi parts of
+// the column potentials and their lo factors (padding: -inf and 0).
+struct ColData {
+    const float4* gc;
+    const float4* cf;
 };
 
 __device__ __forceinline__ float4 exps4(const float4 c, const float4 gg, float kap, float F) {
@@ -232,6 +235,15 @@ __device__ __forceinline__ float dot4(const float4 e, const float4 c, float s) {
     return fmaf(e.x, c.x, fmaf(e.y, c.y, fmaf(e.z, c.z, fmaf(e.w, c.w, s))));
 }
 
+// Compensated (Kahan) addition: sum + c carries the running total of the added
+// values to about one rounding, however many rows a thread accumulates.
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(sum, y);
+    c = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
 // Row update of the two rows of a chunk held by a group (Eq.
 // optimal_f_sinkhorn_logdomain in log2 units): S_r = sum_j 2^(gamma_j - kap c_rj + F_r)
 // around the previous potential F_r, new potential F_r - log2(S_r / alpha_r)
@@ -239,8 +251,8 @@ __device__ __forceinline__ float dot4(const float4 e, const float4 c, float s) {
 // acc.  An explicit max shift is used on the first sweep and whenever a row
 // sum leaves the safe range.
 __device__ __forceinline__ void process_rows(const float* srow, const RowScalars (&R)[2], const BatchArgs& A,
-                                             const SegCtx& X, int row, int k, const ColRegs& CR, float* s_part,
-                                             int& parity, float4 (&acc)[OT_BV], float& l1) {
+                                             const SegCtx& X, int row, int k, const ColData& CR, float* s_part,
+                                             int& parity, float4 (&acc)[OT_BV], float4 (&cmp)[OT_BV], float& l1) {
     if (row >= X.r_hi) return;   // uniform over the group
     const int GS = X.gs, gt = threadIdx.x & (GS - 1), nw = GS >> 5;
     const bool two = row + 1 < X.r_hi;
@@ -260,11 +272,12 @@ __device__ __forceinline__ void process_rows(const float* srow, const RowScalars
             const int g = gt + v * GS;
             e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g < X.ng4) {
-                e0[v] = exps4(c0[g], CR.gc[v], kap, F0);
-                S0 = dot4(e0[v], CR.cf[v], S0);
+                const float4 gg = CR.gc[g], cc = CR.cf[g];
+                e0[v] = exps4(c0[g], gg, kap, F0);
+                S0 = dot4(e0[v], cc, S0);
                 if (two) {
-                    e1[v] = exps4(c1[g], CR.gc[v], kap, F1);
-                    S1 = dot4(e1[v], CR.cf[v], S1);
+                    e1[v] = exps4(c1[g], gg, kap, F1);
+                    S1 = dot4(e1[v], cc, S1);
                 }
             }
         }
@@ -282,7 +295,7 @@ __device__ __forceinline__ void process_rows(const float* srow, const RowScalars
             const int g = gt + v * GS;
             e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g < X.ng4) {
-                const float4 gg = CR.gc[v];
+                const float4 gg = CR.gc[g];
                 float4 c = c0[g];
                 e0[v] = make_float4(fmaf(c.x, -kap, gg.x), fmaf(c.y, -kap, gg.y), fmaf(c.z, -kap, gg.z),
                                     fmaf(c.w, -kap, gg.w));
@@ -306,12 +319,13 @@ __device__ __forceinline__ void process_rows(const float* srow, const RowScalars
                 float4 x = e0[v];
                 x = make_float4(ex2(x.x + F0), ex2(x.y + F0), ex2(x.z + F0), ex2(x.w + F0));
                 e0[v] = x;
-                S0 = dot4(x, CR.cf[v], S0);
+                const float4 cc = CR.cf[g];
+                S0 = dot4(x, cc, S0);
                 if (two) {
                     x = e1[v];
                     x = make_float4(ex2(x.x + F1), ex2(x.y + F1), ex2(x.z + F1), ex2(x.w + F1));
                     e1[v] = x;
-                    S1 = dot4(x, CR.cf[v], S1);
+                    S1 = dot4(x, cc, S1);
                 }
             }
         }
@@ -343,10 +357,10 @@ __device__ __forceinline__ void process_rows(const float* srow, const RowScalars
     }
 #pragma unroll
     for (int v = 0; v < OT_BV; ++v) {
-        acc[v].x = fmaf(u1, e1[v].x, fmaf(u0, e0[v].x, acc[v].x));
-        acc[v].y = fmaf(u1, e1[v].y, fmaf(u0, e0[v].y, acc[v].y));
-        acc[v].z = fmaf(u1, e1[v].z, fmaf(u0, e0[v].z, acc[v].z));
-        acc[v].w = fmaf(u1, e1[v].w, fmaf(u0, e0[v].w, acc[v].w));
+        kahan_add(acc[v].x, cmp[v].x, fmaf(u1, e1[v].x, u0 * e0[v].x));
+        kahan_add(acc[v].y, cmp[v].y, fmaf(u1, e1[v].y, u0 * e0[v].y));
+        kahan_add(acc[v].z, cmp[v].z, fmaf(u1, e1[v].z, u0 * e0[v].z));
+        kahan_add(acc[v].w, cmp[v].w, fmaf(u1, e1[v].w, u0 * e0[v].w));
     }
 }
 
@@ -379,7 +393,7 @@ __device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int NG, in
 // flight.  Returns false (uniformly) if a copy did not complete in time.
 template <int STAGES>
 __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p, int r_lo, int r_hi, int t,
-                             int GS, float* s_part, double isa, Pipe& P) {
+                             int GS, float* s_part, float* s_gc, float* s_cf, double isa, Pipe& P) {
     const int NG = OT_BT / GS;
     const int tid = threadIdx.x, gt = tid & (GS - 1), q = tid / GS;
     SegCtx X;
@@ -404,25 +418,21 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
         for (int k = 0; k < nchunks && k < STAGES; ++k) issue_chunk<STAGES>(P, X, NG, k);
     }
     long long issued = P.consumed + min(nchunks, STAGES);   // block-uniform copy of P.issued
-    // this thread's columns: 4 (gt + v GS) .. + 3
-    ColRegs CR;
-#pragma unroll
-    for (int v = 0; v < OT_BV; ++v) {
-        const int j = 4 * (gt + v * GS);
-        float gv[4], cv[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const bool in = j + c < X.m;
-            gv[c] = in ? A.gc[X.v0 + j + c] : -INFINITY;
-            cv[c] = in ? A.cf[X.v0 + j + c] : 0.f;
-        }
-        CR.gc[v] = make_float4(gv[0], gv[1], gv[2], gv[3]);
-        CR.cf[v] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+    // stage the column data (every thread has finished with the previous segment's)
+    __syncthreads();
+    for (int j = tid; j < X.ld; j += OT_BT) {
+        const bool in = j < X.m;
+        s_gc[j] = in ? A.gc[X.v0 + j] : -INFINITY;
+        s_cf[j] = in ? A.cf[X.v0 + j] : 0.f;
     }
+    __syncthreads();
+    ColData CR;
+    CR.gc = reinterpret_cast<const float4*>(s_gc);
+    CR.cf = reinterpret_cast<const float4*>(s_cf);
     int parity = 0;
-    float4 acc[OT_BV];
+    float4 acc[OT_BV], cmp[OT_BV];   // column contributions (compensated sums)
 #pragma unroll
-    for (int v = 0; v < OT_BV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int v = 0; v < OT_BV; ++v) acc[v] = cmp[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     float l1 = 0.f;
     RowScalars cur[2], nxt[2];
 #pragma unroll
@@ -446,7 +456,7 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
         // that every thread of a group meets the group's barriers; the block then
         // leaves together on the decision below
         process_rows(P.stage + (size_t)st * 2 * OT_BATCH_MAXM + (size_t)(2 * q) * X.ld, cur, A, X, row, k, CR,
-                     s_part, parity, acc, l1);
+                     s_part, parity, acc, cmp, l1);
         // every thread has read the stage (its exponentials are in registers): refill it
         if (__syncthreads_or(!got)) {
             ok = false;
@@ -468,13 +478,13 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
         for (int v = 0; v < OT_BV; ++v) {
             const int g = gt + v * GS;
             if (g < X.ng4) {
-                const float4 cc = CR.cf[v];
+                const float4 cc = CR.cf[g];
                 const int j = 4 * g;
                 const long long o = X.v0 + j;
-                if (j < X.m) red_add_f32(A.R + o, acc[v].x * cc.x);
-                if (j + 1 < X.m) red_add_f32(A.R + o + 1, acc[v].y * cc.y);
-                if (j + 2 < X.m) red_add_f32(A.R + o + 2, acc[v].z * cc.z);
-                if (j + 3 < X.m) red_add_f32(A.R + o + 3, acc[v].w * cc.w);
+                if (j < X.m) red_add_f32(A.R + o, (acc[v].x - cmp[v].x) * cc.x);
+                if (j + 1 < X.m) red_add_f32(A.R + o + 1, (acc[v].y - cmp[v].y) * cc.y);
+                if (j + 2 < X.m) red_add_f32(A.R + o + 2, (acc[v].z - cmp[v].z) * cc.z);
+                if (j + 3 < X.m) red_add_f32(A.R + o + 3, (acc[v].w - cmp[v].w) * cc.w);
             }
         }
     }
@@ -486,6 +496,8 @@ template <int STAGES>
 __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(128) unsigned char dsm[];
     float* s_stage = reinterpret_cast<float*>(dsm + BatchSmem::stage);                 // [STAGES][2 MAXM]
+    float* s_gc = reinterpret_cast<float*>(dsm + BatchSmem::gc);                       // [MAXM]
+    float* s_cf = reinterpret_cast<float*>(dsm + BatchSmem::cf);                       // [MAXM]
     long long* s_pref = reinterpret_cast<long long*>(dsm + BatchSmem::pref);           // [count+1]
     int* s_m = reinterpret_cast<int*>(dsm + BatchSmem::msz);                           // [count]
     int* s_act = reinterpret_cast<int*>(dsm + BatchSmem::act);                         // [count]
@@ -594,7 +606,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 int gs = 32;
                 while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
                 gs = min(OT_BT, gs << A.gs_shift);   // tuned: a larger group takes fewer slots per thread
-                if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, isa, P)) {
+                if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, isa, P)) {
                     if (tid == 0) set_status(A.ctrl, OT_ERR_TIMEOUT);
                     goto fail;
                 }
@@ -843,32 +855,30 @@ extern "C" int ot_batch_fold(int count, const float* points, float* G_all, void*
 // ---- launch configurations and the autotuner
 //
 // A configuration code (ot_options.tile_override for the batch solver) packs
-// the pipeline depth, the group-size policy and the convergence-check cadence:
-// 0 is the default (3 stages, tight groups, opt->check_every); otherwise
-// code - 1 = s | (g << 1) | (c << 2) with s = 0 for 3 stages and 1 for 2,
-// g = group-size shift, c = log2 of the check cadence (0..2).
+// the group-size policy and the convergence-check cadence: 0 is the default
+// (tight groups, opt->check_every); otherwise code - 1 = g | (c << 1) with
+// g = group-size shift and c = log2 of the check cadence (0..2).
 struct BatchCfg {
     int stages, gs_shift, check_every;
 };
 
 static bool decode_cfg(int code, int opt_check_every, BatchCfg& c) {
+    c.stages = OT_STAGES_MAX;
     if (code == 0) {
-        c.stages = 3;
         c.gs_shift = 0;
         c.check_every = opt_check_every >= 1 ? opt_check_every : 1;
         return true;
     }
     code -= 1;
     if (code < 0 || code >= OT_BATCH_NCFG) return false;
-    c.stages = (code & 1) ? 2 : 3;
-    c.gs_shift = (code >> 1) & 1;
-    c.check_every = 1 << (code >> 2);
+    c.gs_shift = code & 1;
+    c.check_every = 1 << (code >> 1);
     return true;
 }
 
 static int encode_cfg(const BatchCfg& c) {
     const int ce = c.check_every >= 4 ? 2 : (c.check_every >= 2 ? 1 : 0);
-    return 1 + ((c.stages == 2) ? 1 : 0) + (c.gs_shift << 1) + (ce << 2);
+    return 1 + c.gs_shift + (ce << 1);
 }
 
 template <int STAGES>
@@ -932,7 +942,7 @@ static int batch_solve_cfg(int count, long long total_m, const float* G_all, con
     A.cf = (float*)(base + L.cf);
     A.R = (float*)(base + L.R);
     if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return OT_ERR_CUDA;
-    return C.stages == 2 ? launch_batch<2>(A, st) : launch_batch<3>(A, st);
+    return launch_batch<OT_STAGES_MAX>(A, st);
 }
 
 static int batch_check_args(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
@@ -1028,17 +1038,17 @@ extern "C" int ot_batch_autotune(int count, long long total_m, const float* G_al
         ms = best;
         return OT_OK;
     };
-    // 1. pipeline depth and group-size policy: a few full sweeps (no problem stops early)
+    // 1. group-size policy: a few full sweeps (no problem stops early)
     ot_options o = *opt;
     o.warm_start = 0;
     o.tol_l1 = 0.0;
     o.max_iter = 4;
     BatchCfg best;
-    best.stages = 3;
+    best.stages = OT_STAGES_MAX;
     best.gs_shift = 0;
     best.check_every = 1;
     float best_ms = 3.4e38f;
-    for (int code = 1; code <= 4 && rc == OT_OK; ++code) {
+    for (int code = 1; code <= 2 && rc == OT_OK; ++code) {
         BatchCfg C;
         decode_cfg(code, 1, C);
         float ms = 0.f;
@@ -1059,7 +1069,7 @@ extern "C" int ot_batch_autotune(int count, long long total_m, const float* G_al
         C.check_every = ce;
         float ms = 0.f;
         rc = timed(C, o, ms);
-        if (ms_out) ms_out[4 + (ce == 1 ? 0 : (ce == 2 ? 1 : 2))] = ms;
+        if (ms_out) ms_out[2 + (ce == 1 ? 0 : (ce == 2 ? 1 : 2))] = ms;
         if (rc == OT_OK && ms < best_full) {
             best_full = ms;
             best_ce = ce;

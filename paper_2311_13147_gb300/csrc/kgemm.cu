@@ -381,8 +381,8 @@ static int kd_gemm(const CUtensorMap& mapA, const CUtensorMap& mapX, int mp, flo
     const int sms = device_sms();
     if (sms <= 0) return OT_ERR_CUDA;
     const int tiles = mp / KD_BM, nkb = mp / KD_BK;
-    // split the reduction so that about two CTAs per SM stream the matrix
-    int splits = (2 * sms + tiles - 1) / tiles;
+    // split the reduction so that the grid fills the two resident CTAs per SM in one wave
+    int splits = (2 * sms) / tiles;
     splits = splits < 1 ? 1 : (splits > nkb ? nkb : splits);
     const int per = (nkb + splits - 1) / splits;
     splits = (nkb + per - 1) / per;   // every slice non-empty

@@ -382,7 +382,7 @@ def ot_batch_autotune(count: int, total_m: int, G_all, a_all, b_all, opt: ot_opt
                       workspace_t, stream=None):
     """Returns (configuration code, measured candidate times in ms)."""
     code = ctypes.c_int(0)
-    ms = (ctypes.c_float * 7)()
+    ms = (ctypes.c_float * 5)()
     rc = _batch_lib().ot_batch_autotune(int(count), int(total_m), _ptr(G_all), _ptr(a_all), _ptr(b_all),
                                         ctypes.byref(opt), _ptr(w_all), _ptr(z_all), _ptr(results),
                                         _ptr(workspace_t), workspace_t.numel(), _stream(stream), ctypes.byref(code), ms)

@@ -146,14 +146,14 @@ def test_batch_autotune_and_configurations(cy):
     tol = 1e-6
     bs = BatchSolver(list(probs), tol=tol)
     iters = {}
-    for code in range(1, 13):
+    for code in range(1, 7):
         bs.opt.tile_override = code
         bs.w.zero_()
         bs.z.zero_()
         bs.run()
         torch.cuda.synchronize()
         res = bs.results()
-        cadence = 1 << ((code - 1) >> 2)
+        cadence = 1 << ((code - 1) >> 1)
         for idx, r in enumerate(res):
             assert r["status"] == cy.OT_OK, (code, idx, r)
             assert r["marg_l1"] <= tol
@@ -164,19 +164,19 @@ def test_batch_autotune_and_configurations(cy):
         rl1, cl1 = oracle_marginal_errors(w, z, C, p.a_base, p.b_base, p.eps)
         assert rl1 <= tol + 1e-6 and cl1 <= 1e-6, (code, rl1, cl1)
     # the cadence only delays the stop to the next multiple (up to a rounding flip at the threshold)
-    for code in range(1, 13):
-        base = iters[1 + ((code - 1) & 3)]
-        cadence = 1 << ((code - 1) >> 2)
+    for code in range(1, 7):
+        base = iters[1 + ((code - 1) & 1)]
+        cadence = 1 << ((code - 1) >> 1)
         for a, b in zip(iters[code], base):
             assert b - 1 <= a <= b + cadence, (code, a, b)
     bs.opt.tile_override = 0
     code = bs.autotune()
-    assert 1 <= code <= 12
+    assert 1 <= code <= 6
     res = bs.results()
     assert all(r["status"] == cy.OT_OK for r in res)
     code2, _ = cy.ot_batch_autotune(bs.count, bs.total_m, bs.G, bs.a, bs.b, bs.opt, bs.w, bs.z, bs.res, bs.ws)
     assert code2 == code
     bad = cy.options(1.0, tol=tol)
-    bad.tile_override = 13
+    bad.tile_override = 7
     with pytest.raises(cy.OTError):
         cy.ot_batch_solve(bs.count, bs.total_m, bs.G, bs.a, bs.b, bad, bs.w, bs.z, bs.res, bs.ws)
