@@ -42,6 +42,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2311_13147_gb300.replicas import max_over_ranks  # noqa: E402
+
 METRIC = "reduced vs full EROT solves/sec at 1e-6 marginal error; Sinkhorn sweep HBM GB/s"
 UNIT = "solves/s"
 
@@ -241,10 +243,8 @@ def run_ours(args, rank, world, local_rank):
     t_full_ms = timed(lambda _r=None: full_step(), args.steps, record=None)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([t_red_ms, t_full_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_red_ms, t_full_ms = float(tt[0]), float(tt[1])
+    t_red_ms = max_over_ranks(t_red_ms, device=dev)
+    t_full_ms = max_over_ranks(t_full_ms, device=dev)
     r = cy.read_result(res)
     rf = cy.read_result(fres)
     solve_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev_solve]))
@@ -354,9 +354,11 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- batch workload
 
-def batch_workload(args):
+def batch_workload(args, rank=0):
     from paper_2311_13147_gb300 import inputs as I
-    probs = I.batch_problems(count=512, seed=0, eps_frac=args.eps_frac)
+    from paper_2311_13147_gb300.replicas import rank_seed
+    # weak scaling: every rank solves a batch of its own (rank 0: seed 0)
+    probs = I.batch_problems(count=512, seed=rank_seed(0, rank), eps_frac=args.eps_frac)
     ms = [p.m for p in probs]
     cfg = {"workload": "batch_512_ring_N2-8_n1024-16384", "count": len(probs), "m_min": min(ms), "m_max": max(ms),
            "sum_m2": int(sum(m * m for m in ms)), "eps_frac_of_max_cost": args.eps_frac, "tol_l1": args.tol,
@@ -373,7 +375,7 @@ def run_ours_batch(args, rank, world, local_rank):
 
     B.build()
     torch.cuda.set_device(local_rank)
-    probs, cfg = batch_workload(args)
+    probs, cfg = batch_workload(args, rank)
     bs = BatchSolver(probs, tol=args.tol, max_iter=100000, device=f"cuda:{local_rank}")
     bs.fold()
     code = bs.autotune()
@@ -398,11 +400,7 @@ def run_ours_batch(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=f"cuda:{local_rank}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt[0])
+    t_ms = max_over_ranks(e0.elapsed_time(e1), device=f"cuda:{local_rank}")
     res = bs.results()
     iters = np.array([r["iters"] for r in res])
     # solver kernel alone (eager launch of the same configuration) for the roofline
