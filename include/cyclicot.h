@@ -68,6 +68,16 @@ extern "C" {
 #define OT_ADJ_ENVELOPE       0   /* gradient from the converged potentials                 */
 #define OT_ADJ_UNROLLED       1   /* reverse pass through a fixed number of iterations        */
 
+/* stopping norms (ot_options.stop_norm) of ot_sinkhorn_reduced / _full:
+ * L1_FULL: sum over the n full rows of |T 1 - a| (the reduced solver's
+ *          N sum_i |S 1 - alpha|_i), compared with tol_l1;
+ * L2_ROW:  ||S 1 - alpha||_2 of the problem as solved (mass 1/N marginals for
+ *          the reduced problem, unit mass for the full one): the Stage-1 rule
+ *          of Algorithm 3 (App. F); ot_result.marg_l1 then holds this norm.
+ * The batch and kernel-domain solvers use L1_FULL only. */
+#define OT_STOP_L1_FULL       0
+#define OT_STOP_L2_ROW        1
+
 #define OT_FP32_LOG           0   /* FP32 log-domain iterations (default)                    */
 #define OT_BF16_KERNEL_POLISH 1   /* BF16 kernel-domain GEMM iterations, then FP32 polish    */
 
@@ -99,6 +109,7 @@ typedef struct {
                                        bit 2 (OT_DEBUG_NO_CLUSTER): do not use the
                                        one-barrier-per-sweep (bulk reduce-add) solver;
                                        use the two-barrier one (comparison runs).        */
+    int stop_norm;                  /* OT_STOP_L1_FULL (default) or OT_STOP_L2_ROW          */
 } ot_options;
 
 #define OT_DEBUG_WITHHOLD_ARRIVAL 1
@@ -328,6 +339,29 @@ int ot_batch_solve(int count, long long total_m, const float* G_all, const float
 int ot_batch_autotune(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
                       const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
                       size_t ws_bytes, void* stream, int* config_out, float* ms_out);
+
+/* ---- Algorithm 3 (two-stage, approximate cyclic symmetry) ------------------ */
+
+/*
+ * ot_first_block_row -- C_base[k][i][j] = C[i][k m + j] for the full cost C
+ * [n][n] (n = N m, FP32 row-major): the blocks that define K in Algorithm 3's
+ * Stage 1 (Eq. def_Kij).  C_base: [N][m][m] FP32.  Device pointers, async.
+ */
+int ot_first_block_row(int m, int N, const float* C, float* C_base, void* stream);
+
+/*
+ * ot_block_average -- out_i = (1/N) sum_k v[k m + i] (Algorithm 3, Stage 1:
+ * the reduced marginals of an approximately symmetric input; FP64 sum).
+ * v: [N m] FP32, out: [m] FP32.  Device pointers, async.
+ */
+int ot_block_average(int m, int N, const float* v, float* out, void* stream);
+
+/*
+ * ot_tile_potentials -- g[k m + j] = z[j] for k < N (Algorithm 3, Stage 2
+ * initialisation: the N-fold concatenation of the Stage-1 potential), to pass
+ * as the warm start of ot_sinkhorn_full.  z: [m] FP64, g: [N m] FP64.
+ */
+int ot_tile_potentials(int m, int N, const double* z, double* g, void* stream);
 
 /* ---- form 1: BF16 kernel-domain iterations on the tensor cores ----------- */
 

@@ -951,7 +951,7 @@ static int batch_check_args(int count, long long total_m, const float* G_all, co
     if (count <= 0 || count > OT_BATCH_MAX || total_m <= 0 || !G_all || !a_all || !b_all || !opt || !w_all ||
         !z_all || !results || !workspace)
         return OT_ERR_ARG;
-    if (opt->max_iter < 1 || opt->tol_l1 < 0.0) return OT_ERR_ARG;
+    if (opt->max_iter < 1 || opt->tol_l1 < 0.0 || opt->stop_norm != OT_STOP_L1_FULL) return OT_ERR_ARG;
     if (((uintptr_t)G_all) % 16) return OT_ERR_ARG;   // bulk copies of cost rows need 16-byte alignment
     if (ws_bytes < ot_batch_workspace_bytes(count, total_m) || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
     return OT_OK;

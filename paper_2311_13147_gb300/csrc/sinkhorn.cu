@@ -60,6 +60,8 @@ struct SkArgs {
     const float* b;
     float kappa;                  // 1 / (eps ln 2)
     double unit;                  // eps ln 2 (log2 units -> cost units)
+    int stop_l2;           // 1: stop on the L2 row error (scaled by l2_scale) instead of the L1
+    double l2_scale;       // 1/N for the reduced problem (its row error at the paper's scale)
     double tol;
     int max_iter;
     int check_every;
@@ -180,9 +182,22 @@ __device__ void fail_exit(const SkArgs& A) {
     }
 }
 
+// Row-error term of one row (d = row sum of the current state - alpha_i, unit-mass scale):
+// |d| for the L1 rule, d^2 for the L2 rule.
+__device__ __forceinline__ double row_err_term(const SkArgs& A, float d) {
+    return A.stop_l2 ? (double)d * (double)d : fabs((double)d);
+}
+
+// The stopping norm from the accumulated terms: the full-scale row L1, or the
+// L2 row error at the paper's scale (sqrt of the sum of squares times l2_scale).
+__device__ __forceinline__ double stop_norm(const SkArgs& A, double acc) {
+    return A.stop_l2 ? sqrt(acc) * A.l2_scale : acc;
+}
+
 // Stopping rule on the state after `done` iterations; returns the status or -1 to continue.
 __device__ __forceinline__ int stop_status(const SkArgs& A, int done, double L1) {
     if (done < 1) return -1;
+    L1 = stop_norm(A, L1);
     if (L1 != L1) return OT_ERR_NONFINITE;
     if (done % A.check_every == 0 && L1 <= A.tol) return OT_OK;
     if (done >= A.max_iter) return OT_ERR_NOT_CONVERGED;
@@ -398,7 +413,7 @@ __device__ __forceinline__ bool fused_band(const SkArgs& A, const RowState& RS, 
         double pnew;
         if (!SAFE) {
             // L1 term of the current state: |S * 2^lo - alpha|
-            l1 += fabs((double)fmaf(S, RS.frf[cur * rm + li] - 1.0f, S - alpha));
+            l1 += row_err_term(A, fmaf(S, RS.frf[cur * rm + li] - 1.0f, S - alpha));
             pnew = (double)RS.fhi[cur * rm + li] - (double)lg2(ratio);
         } else {
             pnew = (double)Fsafe - (double)lg2(ratio);
@@ -629,7 +644,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_fused_kernel(SkArgs A, int nst
                 A.f_out[r_beg + li] = RS.phi[cur * A.rows_max + li] * A.unit + A.f_shift;
             for (int j = c_beg + tid; j < c_end; j += OT_BLOCK)
                 A.g_out[j] = s_gam[cur * A.cols_max + (j - c_beg)] * A.unit;
-            if (B == 0) write_result(A, t - 1, stt, L1, OT_VARIANT_FUSED);
+            if (B == 0) write_result(A, t - 1, stt, stop_norm(A, L1), OT_VARIANT_FUSED);
             break;
         }
         trace_mark(A, t, 3);
@@ -901,7 +916,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_bulk_kernel(SkArgs A, int nsta
                 A.f_out[r_beg + li] = RS.phi[cur * A.rows_max + li] * A.unit + A.f_shift;
             for (int j = o_beg + tid; j < o_end; j += OT_BLOCK)
                 A.g_out[j] = ((double)s_ghi[j] + (double)s_glo[j]) * A.unit;
-            if (B == 0) write_result(A, t - 1, stt, L1, OT_VARIANT_BULK);
+            if (B == 0) write_result(A, t - 1, stt, stop_norm(A, L1), OT_VARIANT_BULK);
             break;
         }
 #pragma unroll
@@ -1074,7 +1089,7 @@ __device__ void twopass_row_band(const SkArgs& A, const RowState& RS, int rb, in
         const float alpha = RS.alpha[li];
         double pnew;
         if (!SAFE) {
-            l1 += fabs((double)fmaf(S, RS.frf[cur * rm + li] - 1.0f, S - alpha));
+            l1 += row_err_term(A, fmaf(S, RS.frf[cur * rm + li] - 1.0f, S - alpha));
             pnew = (double)RS.fhi[cur * rm + li] - (double)lg2(S / alpha);
         } else {
             pnew = (double)s_F[tid] - (double)lg2(S / alpha);
@@ -1162,7 +1177,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
             for (int li = tid; li < r_end - r_beg; li += OT_BLOCK)
                 A.f_out[r_beg + li] = RS.phi[cur * A.rows_max + li] * A.unit + A.f_shift;
             for (int j = c_beg + tid; j < c_end; j += OT_BLOCK) A.g_out[j] = A.gam[cur * A.Ncol + j] * A.unit;
-            if (B == 0) write_result(A, t - 1, stt, L1, OT_VARIANT_TWOPASS);
+            if (B == 0) write_result(A, t - 1, stt, stop_norm(A, L1), OT_VARIANT_TWOPASS);
             break;
         }
         // the queue of the next sweep is idle now (every block has left the previous column pass)
@@ -1393,6 +1408,7 @@ int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
 
 static bool opt_ok(const ot_options* o) {
     return o && o->eps > 0.f && o->max_iter >= 1 && o->check_every >= 1 && o->tol_l1 >= 0.0 &&
+           (o->stop_norm == OT_STOP_L1_FULL || o->stop_norm == OT_STOP_L2_ROW) &&
            o->precision == OT_FP32_LOG && o->tile_override == 0;
 }
 
@@ -1408,6 +1424,8 @@ static SkArgs base_args(const ot_options* o) {
     A.timeout_ns = o->timeout_ns ? o->timeout_ns : 10000000000ull;
     A.warm = o->warm_start ? 1 : 0;
     A.debug_flags = o->debug_flags;
+    A.stop_l2 = o->stop_norm == OT_STOP_L2_ROW ? 1 : 0;
+    A.l2_scale = 1.0;
     return A;
 }
 
@@ -1429,6 +1447,7 @@ extern "C" int ot_sinkhorn_reduced(int m, int N, const float* a_base, const floa
     A.b = b_base;
     // the solver runs with unit-mass marginals; the paper's w (mass 1/N) is f - eps log N
     A.f_shift = -(double)opt->eps * log((double)N);
+    A.l2_scale = 1.0 / (double)N;   // L2 rule: the row error of the mass-1/N reduced problem
     A.f_out = w;
     A.g_out = z;
     A.res = out;

@@ -47,6 +47,8 @@ OT_OP_UNROLLED = 3
 OT_DEBUG_WITHHOLD_ARRIVAL = 1
 OT_DEBUG_TRACE = 2
 OT_DEBUG_NO_CLUSTER = 4
+OT_STOP_L1_FULL = 0
+OT_STOP_L2_ROW = 1
 
 EXPORTED = ("ot_version", "ot_status_string", "ot_workspace_bytes", "ot_fold_cost", "ot_sinkhorn_reduced",
             "ot_sinkhorn_reduced_static", "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad")
@@ -62,7 +64,7 @@ class ot_options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("tol_l1", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("precision", ctypes.c_int), ("warm_start", ctypes.c_int),
                 ("timeout_ns", ctypes.c_ulonglong), ("tile_override", ctypes.c_int),
-                ("debug_flags", ctypes.c_int)]
+                ("debug_flags", ctypes.c_int), ("stop_norm", ctypes.c_int)]
 
 
 class ot_result(ctypes.Structure):
@@ -149,9 +151,10 @@ def _check(code: int, where: str):
 
 def options(eps: float, tol: float = 1e-6, max_iter: int = 10000, check_every: int = 1,
             warm_start: bool = False, timeout_ns: int = 0, precision: int = OT_FP32_LOG,
-            tile_override: int = 0, debug_flags: int = 0) -> ot_options:
+            tile_override: int = 0, debug_flags: int = 0, stop_norm: int = 0) -> ot_options:
     return ot_options(float(eps), float(tol), int(max_iter), int(check_every), int(precision),
-                      int(bool(warm_start)), int(timeout_ns), int(tile_override), int(debug_flags))
+                      int(bool(warm_start)), int(timeout_ns), int(tile_override), int(debug_flags),
+                      int(stop_norm))
 
 
 def new_result(device) -> torch.Tensor:
@@ -436,3 +439,59 @@ def ot_kdomain_status(workspace_t, m: int, stream=None) -> int:
 
 def ot_kdomain_product(mp: int, A, X, Dt, stream=None):
     _check(_kd_lib().ot_kdomain_product(int(mp), _ptr(A), _ptr(X), _ptr(Dt), _stream(stream)), "ot_kdomain_product")
+
+
+# ------------------------------------------------------------------ Algorithm 3 helpers
+
+def _ts_lib():
+    L = lib()
+    if not getattr(L, "_ts_ready", False):
+        L.ot_first_block_row.restype = ctypes.c_int
+        L.ot_first_block_row.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.ot_block_average.restype = ctypes.c_int
+        L.ot_block_average.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.ot_tile_potentials.restype = ctypes.c_int
+        L.ot_tile_potentials.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L._ts_ready = True
+    return L
+
+
+def ot_first_block_row(m: int, N: int, C, C_base=None, stream=None):
+    if C_base is None:
+        C_base = torch.empty((N, m, m), dtype=torch.float32, device=C.device)
+    _check(_ts_lib().ot_first_block_row(int(m), int(N), _ptr(C), _ptr(C_base), _stream(stream)), "ot_first_block_row")
+    return C_base
+
+
+def ot_block_average(m: int, N: int, v, out=None, stream=None):
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=v.device)
+    _check(_ts_lib().ot_block_average(int(m), int(N), _ptr(v), _ptr(out), _stream(stream)), "ot_block_average")
+    return out
+
+
+def ot_tile_potentials(m: int, N: int, z, g=None, stream=None):
+    if g is None:
+        g = torch.empty(m * N, dtype=torch.float64, device=z.device)
+    _check(_ts_lib().ot_tile_potentials(int(m), int(N), _ptr(z), _ptr(g), _stream(stream)), "ot_tile_potentials")
+    return g
+
+
+def two_stage(n: int, N: int, a, b, C, eps: float, stage1_l2: float = 1e-3, tol: float = 1e-6,
+              max_iter: int = 100000, stream=None):
+    """Algorithm 3 through the C ABI (every step in the library's kernels).
+
+    Returns (f, g, stage-1 result, stage-2 result); f, g are the full problem's
+    potentials (unit-mass convention of ot_sinkhorn_full).
+    """
+    m = n // N
+    C_base = ot_first_block_row(m, N, C, stream=stream)
+    alpha = ot_block_average(m, N, a, stream=stream)
+    beta = ot_block_average(m, N, b, stream=stream)
+    G, _ = ot_fold_cost(OT_SOFTMIN, m, N, C_base=C_base, eps=eps, stream=stream)
+    o1 = options(eps, tol=stage1_l2, max_iter=max_iter, stop_norm=OT_STOP_L2_ROW)
+    w1, z1, r1 = ot_sinkhorn_reduced(m, N, alpha, beta, G, o1, stream=stream)
+    g0 = ot_tile_potentials(m, N, z1, stream=stream)
+    o2 = options(eps, tol=tol, max_iter=max_iter, warm_start=True)
+    f, g, r2 = ot_sinkhorn_full(n, a, b, C=C, opt=o2, g=g0, stream=stream)
+    return f, g, read_result(r1), read_result(r2)
