@@ -24,6 +24,13 @@ carrying 64 Dirichlet(0.5) histogram pairs; FP32 log-domain solves of all 64
 pairs against BF16 kernel-domain tensor-core iterations plus the FP32 polish,
 both to 1e-6, with objective errors against the FP64 oracle on a sample.
 
+``--workload polar``: the large polar grid, n = 65536 points in the unit disk
+with 16 sectors (m = 4096 = 256 radii x 16 angles per sector), Gaussian-mixture
+marginals, eps = 0.005 max C.  Step = fold of the 16 blocks from coordinates +
+reduced solve + compact unfold (16 x 4096 x 4096) + value and point gradient;
+beside it the full-size Sinkhorn with the cost formed from the 65536
+coordinates on the fly, both to 1e-6.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle
 on a bounded sample of the same workload instead.
 """
@@ -54,7 +61,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="image_grid", choices=["image_grid", "batch", "precision"])
+    ap.add_argument("--workload", default="image_grid", choices=["image_grid", "batch", "precision", "polar"])
+    ap.add_argument("--polar-eps-frac", type=float, default=0.005)
     ap.add_argument("--eps-frac", type=float, default=0.01)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -660,6 +668,119 @@ def run_ours_precision(args, rank, world, local_rank):
     return out
 
 
+# ---------------------------------------------------------------- large polar workload
+
+def run_ours_polar(args, rank, world, local_rank):
+    import torch
+    from paper_2311_13147_gb300 import build as B
+    from paper_2311_13147_gb300 import cyclicot as cy
+    from paper_2311_13147_gb300 import inputs as I
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = I.polar_grid_problem(eps_frac=args.polar_eps_frac)
+    m, N, n, eps = p.m, p.N, p.n, p.eps
+    x = torch.from_numpy(np.asarray(p.x, np.float32)).to(dev)
+    y = torch.from_numpy(np.asarray(p.y, np.float32)).to(dev)
+    X = torch.from_numpy(I.full_points(np.asarray(p.x, np.float64), N).astype(np.float32)).to(dev)
+    a = torch.from_numpy(p.a_base).to(dev)
+    b = torch.from_numpy(p.b_base).to(dev)
+    af = torch.from_numpy((np.tile(p.a_base, N) / N).astype(np.float32)).to(dev)
+    bf = torch.from_numpy((np.tile(p.b_base, N) / N).astype(np.float32)).to(dev)
+    opt = cy.options(eps, tol=args.tol, max_iter=100000)
+    G = torch.empty((m, m), dtype=torch.float32, device=dev)
+    w = torch.empty(m, dtype=torch.float64, device=dev)
+    z = torch.zeros(m, dtype=torch.float64, device=dev)
+    T = torch.empty((N, m, m), dtype=torch.float32, device=dev)
+    d_a = torch.empty(m, device=dev)
+    d_b = torch.empty(m, device=dev)
+    d_x = torch.empty((m, 2), device=dev)
+    d_y = torch.empty((m, 2), device=dev)
+    res, vres, fres = cy.new_result(dev), cy.new_result(dev), cy.new_result(dev)
+    ws = cy.workspace(cy.OT_OP_SINKHORN_REDUCED, m, N, dev, opt)
+    vws = cy.workspace(cy.OT_OP_VALUE_AND_GRAD, m, N, dev)
+    fws = cy.workspace(cy.OT_OP_SINKHORN_FULL, n, 1, dev, opt)
+    f_full = torch.empty(n, dtype=torch.float64, device=dev)
+    g_full = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = []
+
+    def step(record=False):
+        cy.ot_fold_cost(cy.OT_SOFTMIN, m, N, x=x, y=y, eps=eps, G=G)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        z.zero_()
+        cy.ot_sinkhorn_reduced(m, N, a, b, G, opt, w=w, z=z, out=res, ws=ws)
+        if record:
+            e1.record(stream)
+            ev.append((e0, e1))
+        cy.ot_unfold_plan(cy.OT_PLAN_EROT, m, N, w, z=z, x=x, y=y, eps=eps, dense=False, T=T)
+        cy.ot_value_and_grad(m, N, a, b, x=x, y=y, w=w, z=z, eps=eps, out=vres, d_a=d_a, d_b=d_b, d_x=d_x, d_y=d_y,
+                             ws=vws)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # the full solve repeats the reduced iterations (tiled iterates): cap it near that count
+    r_iters = cy.read_result(res)["iters"]
+    opt_full = cy.options(eps, tol=args.tol, max_iter=max(100, 2 * r_iters + 50))
+
+    def full_step():
+        g_full.zero_()
+        cy.ot_sinkhorn_full(n, af, bf, X=X, Y=X, opt=opt_full, f=f_full, g=g_full, out=fres, ws=fws)
+
+    full_step()   # one untimed full solve (the full problem is expensive: one warm-up)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_red = timed(lambda: step(True), args.steps)
+    full_steps = max(1, min(2, args.steps))
+    t_full = timed(full_step, full_steps)
+    clk = clocks.stop()
+    r, rf, rv = cy.read_result(res), cy.read_result(fres), cy.read_result(vres)
+    if r["status"] != cy.OT_OK or rf["status"] != cy.OT_OK:
+        raise RuntimeError(f"polar solves: reduced {r} full {rf}")
+    solve_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+    red_per_s = world * args.steps / (t_red / 1e3)
+    full_per_s = world * full_steps / (t_full / 1e3)
+    alg = 4.0 * m * m * (r["iters"] + 1)
+    peaks, peak_src = load_peaks()
+    gbs = alg / (solve_ms / 1e3) / 1e9
+    return {
+        "metric": METRIC, "value": red_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_red / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": "polar_n65536_N16_m4096", "n": n, "N": N, "m": m, "eps": eps,
+                   "eps_frac_of_max_cost": args.polar_eps_frac, "tol_l1": args.tol,
+                   "cost": "from coordinates (fold and full solve)", "unfold": "compact [16][4096][4096]",
+                   "l2": "not flushed (the 1.07 GB compact plan written every step exceeds L2)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iters": r["iters"], "marg_l1": r["marg_l1"], "value_objective": rv["value"],
+        "full": {"solves_per_s": full_per_s, "ms_per_solve": t_full / full_steps, "iters": rf["iters"],
+                 "marg_l1": rf["marg_l1"], "cost": "on the fly from 65536 coordinates"},
+        "speedup_reduced_vs_full": red_per_s / full_per_s,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "reduced solver sweep (4 m^2 bytes of the folded cost per sweep; 64 MB, L2-resident)",
+                     "resident": "the 64 MB folded cost fits in L2: the sweep is not HBM-bound at this size",
+                     "solve_ms": solve_ms},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -677,6 +798,11 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.workload == "polar":
+        out = run_ours_polar(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.workload == "precision":
         out = run_ours_precision(args, rank, world, local_rank)
         if rank == 0:

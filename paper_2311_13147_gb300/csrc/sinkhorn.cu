@@ -1055,9 +1055,9 @@ __device__ void twopass_row_band(const SkArgs& A, const RowState& RS, int rb, in
 #pragma unroll
         for (int r = 0; r < WR; ++r) F[r] = s_F[r];
     }
-    float s[WR];
+    float s[WR], sc[WR];   // compensated sums: up to n / OT_BLOCK terms per thread
 #pragma unroll
-    for (int r = 0; r < WR; ++r) s[r] = 0.f;
+    for (int r = 0; r < WR; ++r) s[r] = sc[r] = 0.f;
     for (int j = tid; j < A.Ncol; j += OT_BLOCK) {
         const float g = gcp[j], cfj = cfp[j];
         float2 yj = make_float2(0.f, 0.f);
@@ -1072,13 +1072,13 @@ __device__ void twopass_row_band(const SkArgs& A, const RowState& RS, int rb, in
                 } else {
                     c = __ldg(crow[r] + j);
                 }
-                s[r] += ex2(fmaf(c, -A.kappa, g) + F[r]) * cfj;
+                kahan_add(s[r], sc[r], ex2(fmaf(c, -A.kappa, g) + F[r]) * cfj);
             }
         }
     }
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
-        const float v = warp_sum(s[r]);
+        const float v = warp_sum(s[r] - sc[r]);
         if (lane == 0) s_red[wid][r] = v;
     }
     __syncthreads();
@@ -1197,7 +1197,7 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
             const bool jv = j < A.Ncol;
             const float g = jv ? A.gc[cur * A.Ncol + j] : 0.f;
             const float2 yj = (OTF && jv) ? __ldg(A.Y + j) : make_float2(0.f, 0.f);
-            float s = 0.f;
+            float s = 0.f, sc = 0.f;   // compensated: n / OT_WARPS terms per thread
             if (jv) {
                 for (int i = wid; i < A.M; i += OT_WARPS) {
                     float c;
@@ -1208,10 +1208,10 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_twopass_kernel(SkArgs A) {
                     } else {
                         c = __ldg(A.C + (long long)i * A.ld + j);
                     }
-                    s += ex2(fmaf(c, -A.kappa, fh[i]) + g) * fr[i];
+                    kahan_add(s, sc, ex2(fmaf(c, -A.kappa, fh[i]) + g) * fr[i]);
                 }
             }
-            s_col[wid][lane] = s;
+            s_col[wid][lane] = s - sc;
             __syncthreads();
             if (wid == 0) {
                 int bad = 0;
