@@ -764,6 +764,12 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(const ot_problem_desc* 
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Writes a one-problem table into the workspace from kernel parameters (no host copy, so a single-problem
+// solve through this kernel stays capturable in a CUDA graph).
+__global__ void batch_single_table_kernel(ot_problem_desc d, ot_problem_desc* dst) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = d;
+}
+
 struct BatchLayout {
     size_t ctrl, desc, inv_sa, inv_sb, active, iters, l1acc, flo, fhi, frf, gam, gc, cf, R, total;
 };
@@ -968,6 +974,35 @@ extern "C" int ot_batch_solve(int count, long long total_m, const float* G_all, 
     return batch_solve_cfg(count, total_m, G_all, a_all, b_all, opt, w_all, z_all, results, workspace, ws_bytes,
                            (cudaStream_t)stream, C);
 }
+
+namespace cyc {
+
+// One stored-cost problem through the streaming batch kernel (used by the single-problem
+// solvers for rows of 4097..8192 columns, where the cost cannot stay in shared memory).
+// The potentials follow the batch convention: w = row potential - eps ln N, z = column potential.
+size_t batch_single_ws_bytes(int m) { return ot_batch_workspace_bytes(1, m); }
+
+int batch_single_solve(int m, int N, const float* G, int ld, const float* a, const float* b, const ot_options* opt,
+                       double* w, double* z, ot_result* out, void* workspace, size_t ws_bytes, cudaStream_t st) {
+    if (m <= 0 || m > OT_BATCH_MAXM || ld < m || ld % 4 != 0 || ld > OT_BATCH_MAXM) return OT_ERR_UNSUPPORTED;
+    const int rc = batch_check_args(1, m, G, a, b, opt, w, z, out, workspace, ws_bytes);
+    if (rc != OT_OK) return rc;
+    ot_problem_desc d;
+    memset(&d, 0, sizeof(d));
+    d.m = m;
+    d.N = N;
+    d.eps = opt->eps;
+    d.ld = ld;
+    char* base = (char*)workspace + a256(sizeof(BatchHeader));
+    const BatchLayout L = batch_layout(1, m);
+    batch_single_table_kernel<<<1, 32, 0, st>>>(d, (ot_problem_desc*)(base + L.desc));
+    if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
+    BatchCfg C;
+    decode_cfg(0, opt->check_every, C);
+    return batch_solve_cfg(1, m, G, a, b, opt, w, z, out, workspace, ws_bytes, st, C);
+}
+
+}  // namespace cyc
 
 namespace {
 std::mutex g_tune_mu;

@@ -1294,11 +1294,18 @@ static bool fused_ok(const SkArgs& A, int grid) {
            (A.Ncol + grid - 1) / grid <= kFusedMaxRowsPerBlock;
 }
 
+size_t batch_single_ws_bytes(int m);
+
 size_t solver_ws_bytes(int M, int Ncol, bool stored) {
     const bool fused = stored && Ncol <= kFusedMaxCols;   // partial buffer sized whenever it may be used
     const int grid = solver_grid(M);
     if (grid <= 0) return 0;
-    return ws_layout(M, Ncol, grid, fused).total;
+    size_t b = ws_layout(M, Ncol, grid, fused).total;
+    if (stored && M == Ncol && Ncol > kFusedMaxCols && Ncol <= 8192) {   // the streaming route
+        const size_t s = batch_single_ws_bytes(Ncol);
+        b = s > b ? s : b;
+    }
+    return b;
 }
 
 template <typename K, typename... Args>
@@ -1358,6 +1365,18 @@ static int launch_bulk(SkArgs& A, int grid, cudaStream_t st) {
     if (cpt <= 4) return rows_max <= 8 ? launch_bulk_r<4, 8>(A, grid, st) : launch_bulk_r<4, 16>(A, grid, st);
     if (cpt <= 8) return launch_bulk_r<8, 8>(A, grid, st);
     return launch_bulk_r<16, 4>(A, grid, st);
+}
+
+size_t batch_single_ws_bytes(int m);
+int batch_single_solve(int m, int N, const float* G, int ld, const float* a, const float* b, const ot_options* opt,
+                       double* w, double* z, ot_result* out, void* workspace, size_t ws_bytes, cudaStream_t st);
+
+// A square stored cost too wide for the resident kernels (4096 < columns <= 8192,
+// rows 16-byte aligned) streams through the batch kernel: bulk-copy pipeline,
+// one read of the cost per sweep, compensated column sums.
+static bool streaming_ok(const SkArgs& A, int grid, const ot_options* o) {
+    return A.C != nullptr && !fused_ok(A, grid) && A.M == A.Ncol && A.Ncol > kFusedMaxCols && A.Ncol <= 8192 &&
+           A.ld % 4 == 0 && ((uintptr_t)A.C) % 16 == 0 && o->stop_norm == OT_STOP_L1_FULL && o->debug_flags == 0;
 }
 
 int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
@@ -1451,6 +1470,10 @@ extern "C" int ot_sinkhorn_reduced(int m, int N, const float* a_base, const floa
     A.f_out = w;
     A.g_out = z;
     A.res = out;
+    const int grid = solver_grid(A.M);
+    if (grid > 0 && streaming_ok(A, grid, opt))
+        return batch_single_solve(m, N, G, m, a_base, b_base, opt, w, z, out, workspace, ws_bytes,
+                                  (cudaStream_t)stream);
     return run_solver(A, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -1473,5 +1496,8 @@ extern "C" int ot_sinkhorn_full(int n, const float* a, const float* b, const flo
     A.f_out = f;
     A.g_out = g;
     A.res = out;
+    const int grid = solver_grid(A.M);
+    if (grid > 0 && streaming_ok(A, grid, opt))
+        return batch_single_solve(n, 1, C, n, a, b, opt, f, g, out, workspace, ws_bytes, (cudaStream_t)stream);
     return run_solver(A, workspace, ws_bytes, (cudaStream_t)stream);
 }

@@ -168,7 +168,7 @@ def read_result(res: torch.Tensor) -> dict:
     r = ot_result.from_buffer_copy(raw)
     return {"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1, "marg_l2_col": r.marg_l2_col,
             "value": r.value, "transport_cost": r.transport_cost, "marg_l1_col": r.marg_l1_col,
-            "mass": r.reserved[0], "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass"}.get(r.reserved[1], "other")}
+            "mass": r.reserved[0], "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream"}.get(r.reserved[1], "other")}
 
 
 def ot_workspace_bytes(op: int, m_or_n: int, N: int, opt: Optional[ot_options] = None) -> int:

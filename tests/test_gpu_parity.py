@@ -375,3 +375,42 @@ def test_solver_variants_agree(cy):
     Gq, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, q.m, q.N, C_base=dev(q.C_base), eps=q.eps)
     _, _, o3 = cy.ot_sinkhorn_reduced(q.m, q.N, dev(q.a_base), dev(q.b_base), Gq, cy.options(q.eps, tol=1e-6))
     assert cy.read_result(o3)["variant"] == "twopass"
+
+
+@pytest.mark.parametrize("m,N,seed", [(4100, 2, 0), (6000, 2, 1)])
+def test_reduced_streaming_route_parity(cy, m, N, seed):
+    """Rows wider than the resident kernels take (4097..8192 columns) stream through the batch kernel."""
+    p = I.sector_problem(m, N, seed=seed, eps_frac=0.05)
+    tol = 1e-6
+    Cb, G, w, z, res = _solve_reduced(cy, p, tol)
+    assert res["status"] == cy.OT_OK, res
+    assert res["variant"] == "stream"
+    assert res["marg_l1"] <= tol
+    wg, zg = host(w), host(z)
+    rl1, cl1 = fp64_row_col_errors(wg, zg, p.C_base, p.a_base, p.b_base, p.eps)
+    assert rl1 <= tol + 1e-6 and cl1 <= 1e-6, (rl1, cl1)
+    orc = OS.cyclic_sinkhorn(p.a_base, p.b_base, p.C_base, p.eps, tol=tol)
+    assert abs(res["iters"] - orc["iters"]) <= 0.03 * orc["iters"] + 2, (res["iters"], orc["iters"])
+    d = wg - orc["w"]
+    assert np.abs(d - d.mean()).max() <= 1e-4 * p.eps + 1e-5 * np.abs(orc["w"]).max()
+
+
+def test_full_streaming_route_warm_start(cy):
+    """A full problem of n = 4400 (stored cost) through the streaming route, cold and warm."""
+    p = I.sector_problem(1100, 4, seed=4, eps_frac=0.05)
+    C = I.full_cost_from_blocks(p.C_base)
+    a = np.tile(p.a_base, p.N)
+    b = np.tile(p.b_base, p.N)
+    tol = 1e-6
+    f, g, out = cy.ot_sinkhorn_full(p.n, dev(a), dev(b), C=dev(C), opt=cy.options(p.eps, tol=tol))
+    res = cy.read_result(out)
+    assert res["status"] == cy.OT_OK and res["variant"] == "stream"
+    fg, gg = host(f), host(g)
+    T = np.exp((fg[:, None] + gg[None, :] - C.astype(np.float64)) / p.eps)
+    e = OR.marginal_errors(T, OS.normalise(a), OS.normalise(b))
+    assert e["row_l1"] <= tol + 1e-6 and e["col_l1"] <= 1e-6, e
+    # warm start from the converged g: stops after the first measured sweep
+    f2, g2, out2 = cy.ot_sinkhorn_full(p.n, dev(a), dev(b), C=dev(C), opt=cy.options(p.eps, tol=tol, warm_start=True),
+                                       g=g.clone())
+    r2 = cy.read_result(out2)
+    assert r2["status"] == cy.OT_OK and r2["iters"] <= 2
