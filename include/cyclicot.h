@@ -397,10 +397,12 @@ int ot_kdomain_status(const void* workspace, int m, int* status, void* stream);
  * ot_kdomain_product -- the tensor-core product used by ot_kdomain_solve:
  * Dt[n][i] = sum_k A[i][k] X[n][k] for n < 64, i < mp; A [mp][mp] BF16,
  * X [64][mp] BF16, Dt [64][mp] FP32 (device, 16-byte aligned; mp a multiple
- * of 128, <= 16384).  Blocks until done; returns OT_ERR_TIMEOUT if a device
- * wait expired.
+ * of 128, <= 16384).  workspace: >= ot_kdomain_workspace_bytes(mp) bytes
+ * (256-byte aligned; holds the partial products of the reduction slices).
+ * Blocks until done; returns OT_ERR_TIMEOUT if a device wait expired.
  */
-int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* stream);
+int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* workspace, size_t ws_bytes,
+                       void* stream);
 
 #ifdef __cplusplus
 }

@@ -19,8 +19,9 @@
 //   thread 32     MMA issuer: 4 tcgen05.mma (M 128, N 64, K 16, BF16 -> FP32)
 //                 per stage, then tcgen05.commit frees the stage;
 //   all 4 warps   epilogue: tcgen05.ld of the 128 x 64 FP32 accumulator (warp w
-//                 reads lanes 32w..32w+31) and FP32 reductions into the output,
-//                 stored [64][mp] (one row per right-hand side).
+//                 reads lanes 32w..32w+31), stored as this reduction slice's
+//                 partial product [64][mp] (one row per right-hand side); the
+//                 scaling update sums the slices.
 // Every wait is bounded; an expired wait sets an error flag and the CTA still
 // frees its tensor memory.
 #include <cuda.h>
@@ -42,6 +43,7 @@ int device_sms();
 #define KD_B_BYTES (KD_BN * KD_BK * 2)
 #define KD_STAGE_BYTES (KD_A_BYTES + KD_B_BYTES)
 #define KD_SMEM (KD_STAGES * KD_STAGE_BYTES + 1024)
+#define KD_MAX_SPLITS 16           // reduction slices (each stores its own partial product)
 
 // ---- tcgen05 / TMA helpers (inline PTX)
 
@@ -109,19 +111,15 @@ __device__ __forceinline__ unsigned long long smem_desc_sw128(const void* tile) 
 // bits [17,23), M >> 4 in bits [24,29).
 #define KD_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(KD_BN >> 3) << 17) | ((unsigned)(KD_BM >> 4) << 24))
 
-__device__ __forceinline__ void red_add_f32(float* p, float v) {
-    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-
 struct GemmArgs {
     int mp;                       // padded size (multiple of 128)
     int kb_per_split;             // reduction blocks (of 64) per CTA slice
-    float* Dt;                    // [64][mp] output, accumulated (zeroed by the caller)
+    float* Dp;                    // [splits][64][mp] partial products, one slice per blockIdx.y
     int* err;                     // error flag (OT_ERR_TIMEOUT on an expired wait)
     unsigned long long timeout_ns;
 };
 
-// Dt[n][i] += sum_k A[i][k] X[n][k] over this CTA's rows i and reduction slice.
+// Dp[s][n][i] = sum over slice s of k of A[i][k] X[n][k] for this CTA's rows i.
 // A: tensor map of a [mp][mp] BF16 matrix (row-major, K-major operand);
 // X: tensor map of the [64][mp] BF16 scaling vectors (K-major operand).
 __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -207,7 +205,8 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
             float v[16];
             tmem_ld16(taddr + 16 * c, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) red_add_f32(g.Dt + (size_t)(16 * c + j) * g.mp + row, v[j]);
+            for (int j = 0; j < 16; ++j)
+                g.Dp[((size_t)blockIdx.y * KD_BN + 16 * c + j) * g.mp + row] = v[j];   // coalesced over lanes
         }
     }
     tc_fence_before();
@@ -283,16 +282,20 @@ __global__ void __launch_bounds__(256) kd_prep_kernel(const float* __restrict__ 
     }
 }
 
-// X = H ./ D (0 where D = 0 or outside the problem); err[n] += sum_i |Xold_i D_i - H_i|,
+// X = H ./ D with D the sum of the product's reduction slices (0 where D = 0 or
+// outside the problem); err[n] += sum_i |Xold_i D_i - H_i|,
 // the L1 marginal error of the state before this half-iteration on this side.
-__global__ void __launch_bounds__(256) kd_scale_kernel(const float* __restrict__ D, const float* __restrict__ H,
-                                                       float* __restrict__ X, __nv_bfloat16* __restrict__ Xt, int m,
-                                                       int mp, float* __restrict__ err) {
+__global__ void __launch_bounds__(256) kd_scale_kernel(const float* __restrict__ Dp, int splits,
+                                                       const float* __restrict__ H, float* __restrict__ X,
+                                                       __nv_bfloat16* __restrict__ Xt, int m, int mp,
+                                                       float* __restrict__ err) {
     const int n = blockIdx.y;
     float e = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x) {
         const size_t o = (size_t)n * mp + i;
-        const float d = D[o], h = H[o];
+        float d = 0.f;   // the product: sum of the reduction slices
+        for (int sl = 0; sl < splits; ++sl) d += Dp[(size_t)sl * KD_BN * mp + o];
+        const float h = H[o];
         if (err) e += fabsf(fmaf(X[o], d, -h));
         const float x = (i < m && d > 0.f && h > 0.f) ? __fdiv_rn(h, d) : 0.f;
         X[o] = x;
@@ -335,7 +338,7 @@ static KdLayout kd_layout(int mp) {
     L.V = o; o = a256(o + 4 * vn);
     L.Ut = o; o = a256(o + 2 * vn);
     L.Vt = o; o = a256(o + 2 * vn);
-    L.D = o; o = a256(o + 4 * vn);
+    L.D = o; o = a256(o + 4 * vn * KD_MAX_SPLITS);
     L.err = o; o = a256(o + 4 * (size_t)KD_BN);
     L.flag = o; o = a256(o + 64);
     L.total = o;
@@ -375,24 +378,30 @@ static bool make_map(CUtensorMap* map, void* base, int rows, int cols, int box_r
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Dt = A X^T for the [mp][mp] BF16 matrix behind mapA.
-static int kd_gemm(const CUtensorMap& mapA, const CUtensorMap& mapX, int mp, float* Dt, int* flag,
-                   unsigned long long timeout_ns, cudaStream_t st) {
+// Reduction slices of the product for size mp (the grid fills two resident CTAs per SM in one wave).
+static int kd_splits(int mp) {
     const int sms = device_sms();
-    if (sms <= 0) return OT_ERR_CUDA;
+    if (sms <= 0) return 0;
     const int tiles = mp / KD_BM, nkb = mp / KD_BK;
-    // split the reduction so that the grid fills the two resident CTAs per SM in one wave
     int splits = (2 * sms) / tiles;
     splits = splits < 1 ? 1 : (splits > nkb ? nkb : splits);
+    splits = splits > KD_MAX_SPLITS ? KD_MAX_SPLITS : splits;
     const int per = (nkb + splits - 1) / splits;
-    splits = (nkb + per - 1) / per;   // every slice non-empty
+    return (nkb + per - 1) / per;   // every slice non-empty
+}
+
+// Partial products Dp[s] (s < kd_splits(mp)) of A X^T for the [mp][mp] BF16 matrix behind mapA.
+static int kd_gemm(const CUtensorMap& mapA, const CUtensorMap& mapX, int mp, float* Dp, int* flag,
+                   unsigned long long timeout_ns, cudaStream_t st) {
+    const int splits = kd_splits(mp);
+    if (splits <= 0) return OT_ERR_CUDA;
+    const int tiles = mp / KD_BM, nkb = mp / KD_BK;
     GemmArgs g;
     g.mp = mp;
-    g.kb_per_split = per;
-    g.Dt = Dt;
+    g.kb_per_split = (nkb + splits - 1) / splits;
+    g.Dp = Dp;
     g.err = flag;
     g.timeout_ns = timeout_ns;
-    if (cudaMemsetAsync(Dt, 0, sizeof(float) * (size_t)KD_BN * mp, st) != cudaSuccess) return OT_ERR_CUDA;
     kd_gemm_kernel<<<dim3(tiles, splits), 128, KD_SMEM, st>>>(mapA, mapX, g);
     return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
 }
@@ -442,13 +451,15 @@ extern "C" int ot_kdomain_solve(int m, const float* G, int ld, float eps, int nr
     if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     const unsigned long long tmo = 10000000000ull;
     const dim3 sgrid((mp + 255) / 256 < 64 ? (mp + 255) / 256 : 64, KD_BN);
+    const int splits = kd_splits(mp);
     for (int it = 0; it < iters; ++it) {
-        int rc = kd_gemm(mK, mV, mp, D, flag, tmo, st);   // D = K V
+        int rc = kd_gemm(mK, mV, mp, D, flag, tmo, st);   // D = K V (in reduction slices)
         if (rc != OT_OK) return rc;
-        kd_scale_kernel<<<sgrid, 256, 0, st>>>(D, alpha, U, Ut, m, mp, row_err ? row_err + (size_t)it * KD_BN : nullptr);
+        kd_scale_kernel<<<sgrid, 256, 0, st>>>(D, splits, alpha, U, Ut, m, mp,
+                                               row_err ? row_err + (size_t)it * KD_BN : nullptr);
         rc = kd_gemm(mKt, mU, mp, D, flag, tmo, st);       // D = K^T U
         if (rc != OT_OK) return rc;
-        kd_scale_kernel<<<sgrid, 256, 0, st>>>(D, beta, V, Vt, m, mp, nullptr);
+        kd_scale_kernel<<<sgrid, 256, 0, st>>>(D, splits, beta, V, Vt, m, mp, nullptr);
     }
     kd_log_kernel<<<dim3(sgrid.x, KD_BN), 256, 0, st>>>(V, m, mp, nrhs, (double)eps, z_out);
     return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
@@ -468,12 +479,25 @@ extern "C" int ot_kdomain_status(const void* workspace, int m, int* status, void
 
 namespace {
 __device__ int g_kd_product_flag;
+
+__global__ void __launch_bounds__(256) kd_sum_slices_kernel(const float* __restrict__ Dp, int splits, int mp,
+                                                            float* __restrict__ Dt) {
+    const int n = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x) {
+        float d = 0.f;
+        for (int s = 0; s < splits; ++s) d += Dp[((size_t)s * KD_BN + n) * mp + i];
+        Dt[(size_t)n * mp + i] = d;
+    }
+}
 }
 
 // Dt[n][i] = sum_k A[i][k] X[n][k] on the tensor cores (the product inside ot_kdomain_solve).
-extern "C" int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* stream) {
-    if (mp <= 0 || mp % KD_BM != 0 || mp > 16384 || !A || !X || !Dt) return OT_ERR_ARG;
+extern "C" int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* workspace, size_t ws_bytes,
+                                  void* stream) {
+    if (mp <= 0 || mp % KD_BM != 0 || mp > 16384 || !A || !X || !Dt || !workspace) return OT_ERR_ARG;
     if (((uintptr_t)A) % 16 || ((uintptr_t)X) % 16) return OT_ERR_ARG;
+    const KdLayout L = kd_layout(mp);
+    if (ws_bytes < L.total || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     CUtensorMap mA, mX;
     if (!make_map(&mA, (void*)A, mp, mp, KD_BM) || !make_map(&mX, (void*)X, KD_BN, mp, KD_BN)) return OT_ERR_CUDA;
@@ -482,8 +506,14 @@ extern "C" int ot_kdomain_product(int mp, const void* A, const void* X, float* D
     int* flag = nullptr;
     if (cudaGetSymbolAddress((void**)&flag, g_kd_product_flag) != cudaSuccess) return OT_ERR_CUDA;
     if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return OT_ERR_CUDA;
-    const int rc = kd_gemm(mA, mX, mp, Dt, flag, 10000000000ull, st);
+    // the slices go to the workspace's product region, then one pass sums them into Dt
+    const int splits = kd_splits(mp);
+    if (splits <= 0) return OT_ERR_CUDA;
+    float* Dp = (float*)((char*)workspace + L.D);
+    int rc = kd_gemm(mA, mX, mp, Dp, flag, 10000000000ull, st);
     if (rc != OT_OK) return rc;
+    kd_sum_slices_kernel<<<dim3((mp + 255) / 256 < 64 ? (mp + 255) / 256 : 64, KD_BN), 256, 0, st>>>(Dp, splits, mp, Dt);
+    if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

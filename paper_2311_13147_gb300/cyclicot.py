@@ -406,7 +406,7 @@ def _kd_lib():
         L.ot_kdomain_status.restype = ctypes.c_int
         L.ot_kdomain_status.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
         L.ot_kdomain_product.restype = ctypes.c_int
-        L.ot_kdomain_product.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.ot_kdomain_product.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
         L._kd_ready = True
     return L
 
@@ -437,8 +437,11 @@ def ot_kdomain_status(workspace_t, m: int, stream=None) -> int:
     return st.value
 
 
-def ot_kdomain_product(mp: int, A, X, Dt, stream=None):
-    _check(_kd_lib().ot_kdomain_product(int(mp), _ptr(A), _ptr(X), _ptr(Dt), _stream(stream)), "ot_kdomain_product")
+def ot_kdomain_product(mp: int, A, X, Dt, workspace_t=None, stream=None):
+    if workspace_t is None:
+        workspace_t = torch.empty(max(ot_kdomain_workspace_bytes(mp), 256), dtype=torch.uint8, device=Dt.device)
+    _check(_kd_lib().ot_kdomain_product(int(mp), _ptr(A), _ptr(X), _ptr(Dt), _ptr(workspace_t), workspace_t.numel(),
+                                        _stream(stream)), "ot_kdomain_product")
 
 
 # ------------------------------------------------------------------ Algorithm 3 helpers
