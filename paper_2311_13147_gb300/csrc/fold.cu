@@ -11,6 +11,8 @@
 
 namespace cyc {
 
+#define FOLD_U 8   // cost blocks loaded per round of the stored-cost folds
+
 // min with numpy semantics: a NaN propagates and its first index is kept.
 __device__ __forceinline__ void min_step(float c, int k, float& best, int& kb) {
     if (best != best) return;
@@ -36,25 +38,41 @@ __global__ void __launch_bounds__(OT_BLOCK) fold_blocks_vec4(int N, long long mm
         float4 c0 = __ldg(C + e);
         float b[4] = {c0.x, c0.y, c0.z, c0.w};
         int kb[4] = {0, 0, 0, 0};
+        // blocks are loaded FOLD_U at a time (all loads in flight), then folded in order of k
+        float4 cks[FOLD_U];
         if (MODE == OT_MIN) {
-            for (int k = 1; k < N; ++k) {
-                float4 ck = __ldg(C + (long long)k * mm4 + e);
-                min_step(ck.x, k, b[0], kb[0]);
-                min_step(ck.y, k, b[1], kb[1]);
-                min_step(ck.z, k, b[2], kb[2]);
-                min_step(ck.w, k, b[3], kb[3]);
+            for (int k0 = 1; k0 < N; k0 += FOLD_U) {
+#pragma unroll
+                for (int u = 0; u < FOLD_U; ++u)
+                    if (k0 + u < N) cks[u] = __ldg(C + (long long)(k0 + u) * mm4 + e);
+#pragma unroll
+                for (int u = 0; u < FOLD_U; ++u) {
+                    if (k0 + u < N) {
+                        min_step(cks[u].x, k0 + u, b[0], kb[0]);
+                        min_step(cks[u].y, k0 + u, b[1], kb[1]);
+                        min_step(cks[u].z, k0 + u, b[2], kb[2]);
+                        min_step(cks[u].w, k0 + u, b[3], kb[3]);
+                    }
+                }
             }
             G[e] = make_float4(b[0], b[1], b[2], b[3]);
             if (ks) ks[e] = make_uchar4(kb[0], kb[1], kb[2], kb[3]);
         } else {
             // one pass, online soft-min: s = sum_k exp2((mn - C_k) * kappa) for the running minimum mn
             float s[4] = {1.f, 1.f, 1.f, 1.f};
-            for (int k = 1; k < N; ++k) {
-                float4 ck = __ldg(C + (long long)k * mm4 + e);
-                softmin_step(ck.x, kappa, b[0], s[0]);
-                softmin_step(ck.y, kappa, b[1], s[1]);
-                softmin_step(ck.z, kappa, b[2], s[2]);
-                softmin_step(ck.w, kappa, b[3], s[3]);
+            for (int k0 = 1; k0 < N; k0 += FOLD_U) {
+#pragma unroll
+                for (int u = 0; u < FOLD_U; ++u)
+                    if (k0 + u < N) cks[u] = __ldg(C + (long long)(k0 + u) * mm4 + e);
+#pragma unroll
+                for (int u = 0; u < FOLD_U; ++u) {
+                    if (k0 + u < N) {
+                        softmin_step(cks[u].x, kappa, b[0], s[0]);
+                        softmin_step(cks[u].y, kappa, b[1], s[1]);
+                        softmin_step(cks[u].z, kappa, b[2], s[2]);
+                        softmin_step(cks[u].w, kappa, b[3], s[3]);
+                    }
+                }
             }
             const float inv = 1.0f / kappa;
             G[e] = make_float4(b[0] - inv * lg2(s[0]), b[1] - inv * lg2(s[1]),

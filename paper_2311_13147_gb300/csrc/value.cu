@@ -88,6 +88,14 @@ __global__ void __launch_bounds__(OT_BLOCK) value_tiles(VArgs A) {
         }
         float cs = 0.f, cx = 0.f, cy = 0.f;     // column partials over the tile rows
         float tct = 0.f, tta = 0.f, tt = 0.f;  // scalar partials
+        // the tile's stored costs are loaded before any of them is used (all loads in flight)
+        float cpre[VT_R];
+        if (!POINTS) {
+#pragma unroll
+            for (int r = 0; r < VT_R; ++r)
+                cpre[r] = (jv && i0 + r < m) ? __ldg(A.C + (long long)k * m * m + (long long)(i0 + r) * m + j) : 0.f;
+        }
+#pragma unroll
         for (int r = 0; r < VT_R; ++r) {
             const int i = i0 + r;
             float T = 0.f, rx = 0.f, ry = 0.f;
@@ -100,7 +108,7 @@ __global__ void __launch_bounds__(OT_BLOCK) value_tiles(VArgs A) {
                     const float dx = xi.x - ykj.x, dy = xi.y - ykj.y;
                     cst = fmaf(dx, dx, dy * dy);
                 } else {
-                    cst = __ldg(A.C + (long long)k * m * m + e);
+                    cst = cpre[r];
                 }
                 const float arg = fmaf(cst, -A.kappa, s_wh[r] + s_zh[tid]) + (s_wl[r] + s_zl[tid]);
                 T = ex2(arg);
@@ -173,8 +181,9 @@ __global__ void __launch_bounds__(OT_BLOCK) value_finalize(int m, int N, const f
     sa = block_sum_d(sa, s_dred);
     sb = block_sum_d(sb, s_dred);
     double wa = 0.0, zb = 0.0, rl1 = 0.0, cl1 = 0.0, cl2 = 0.0;
+    const double ia = 1.0 / (sa * N), ib = 1.0 / (sb * N);   // one division each (FP64 divides are slow)
     for (int i = tid; i < m; i += OT_BLOCK) {
-        const double al = (double)a[i] / (sa * N), be = (double)b[i] / (sb * N);
+        const double al = (double)a[i] * ia, be = (double)b[i] * ib;
         wa += w[i] * a[i];
         zb += z[i] * b[i];
         rl1 += fabs(rowS[i] - al);
@@ -187,9 +196,10 @@ __global__ void __launch_bounds__(OT_BLOCK) value_finalize(int m, int N, const f
     rl1 = block_sum_d(rl1, s_dred);
     cl1 = block_sum_d(cl1, s_dred);
     cl2 = block_sum_d(cl2, s_dred);
+    const double isa = 1.0 / sa, isb = 1.0 / sb, wm = wa * isa, zm = zb * isb;
     for (int i = tid; i < m; i += OT_BLOCK) {
-        if (d_a) d_a[i] = (float)((w[i] - wa / sa) / sa);
-        if (d_b) d_b[i] = (float)((z[i] - zb / sb) / sb);
+        if (d_a) d_a[i] = (float)((w[i] - wm) * isa);
+        if (d_b) d_b[i] = (float)((z[i] - zm) * isb);
         if (d_x) {
             const double xs = rowS[i];
             d_x[2 * i] = (float)(2.0 * N * (xs * x[i].x - rowP[2 * i]));
