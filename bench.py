@@ -346,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
         # per step: min fold, soft-min fold, reduced solver, unfold, value tiles + finalise
         "gpu_launches": 6 * args.steps,
         "kernels_per_step": ["fold_blocks_vec4<MIN>", "fold_blocks_vec4<SOFTMIN>", "sk_bulk_kernel",
-                             "unfold_kernel<EROT>", "value_tiles", "value_finalize"],
+                             "unfold_erot_vec4", "value_tiles", "value_finalize"],
         "clocks": clk,
     }
     return out, p
