@@ -8,14 +8,19 @@
 //               weighted by row length; every block takes a contiguous,
 //               equally weighted range of it (recomputed identically in every
 //               block each sweep, so finished problems free their share).  A
-//               band of R rows is streamed twice from global memory (float4,
-//               coalesced; the second read hits L1/L2): pass 1 forms the row
-//               sums and the new row potentials, pass 2 the column
-//               contributions u_i * e_ij, accumulated in shared memory per
-//               problem segment and added into the problem's column sums with
-//               FP32 reductions (a problem is split over few blocks, so each
-//               sum receives few terms).  The row L1 terms go to a per-problem
-//               FP64 accumulator.
+//               block streams chunks of rows (two per thread group) through
+//               shared-memory stages filled by bulk copies, together with the
+//               rows' scalars (previous potential, its lo factor, the row
+//               marginal).  A group of GS threads owns a fixed set of
+//               columns; it forms the exponentials of its two rows around the
+//               previous potentials in registers, releases the stage (so that
+//               the next copy starts while the row sums are reduced), then
+//               writes the new row potentials and adds the column
+//               contributions u_i e_ij to compensated sums in registers.  At
+//               the end of a problem segment these are added into the
+//               problem's column sums with FP32 reductions (a problem is split
+//               over few blocks, so each sum receives few terms).  The row L1
+//               terms go to a per-problem FP64 accumulator.
 //  column phase The columns of the active problems are split the same way;
 //               each column's potential is updated from its sum (FP64), the
 //               sum is cleared, and the block holding a problem's column 0
@@ -68,9 +73,9 @@ struct BatchArgs {
     int* active;                   // [count]
     int* iters;                    // [count]
     double* l1acc;                 // [2][count]
-    float* flo;                    // [2][total_m] row potential = fhi + flo (exactly), log2 units
-    float* fhi;                    // [2][total_m]
-    float* frf;                    // [2][total_m] 2^flo
+    float4* rs;                    // [2][total_m] row scalars {hi part of the row potential (log2 units),
+                                   //  2^lo, alpha_i = a_i / sum a, 0}; the potential is hi + lo exactly
+    float* flo;                    // [2][total_m] lo part of the row potential
     double* gam;                   // [total_m]
     float* gc;                     // [total_m]
     float* cf;                     // [total_m]
@@ -78,12 +83,13 @@ struct BatchArgs {
 };
 
 // Dynamic shared memory of the solver: OT_STAGES_MAX chunk stages (two rows per
-// group) filled by bulk copies, the current problem's staged column data,
-// prefix sums, block sizes and active flags.
+// group, and their rows' scalars) filled by bulk copies, the current problem's
+// staged column data, prefix sums, block sizes and active flags.
 constexpr size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 struct BatchSmem {
     static constexpr size_t stage = 0;
-    static constexpr size_t gc = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES_MAX);
+    static constexpr size_t rsc = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES_MAX);
+    static constexpr size_t gc = a128(rsc + sizeof(float4) * 2 * OT_BW * OT_STAGES_MAX);
     static constexpr size_t cf = a128(gc + sizeof(float) * OT_BATCH_MAXM);
     static constexpr size_t pref = a128(cf + sizeof(float) * OT_BATCH_MAXM);
     static constexpr size_t msz = a128(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
@@ -95,6 +101,70 @@ static_assert(BatchSmem::total + 2048 <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void red_add_f32(float* p, float v) {
     asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+// ---- packed FP32 pairs (f32x2 instructions: two lanes of arithmetic per instruction)
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Compensated (Kahan) addition on both lanes: sum + c carries the running total of
+// the added values to about one rounding, however many rows a thread accumulates.
+__device__ __forceinline__ void kahan2(f32x2& sum, f32x2& c, f32x2 v) {
+    const f32x2 y = sub2(v, c);
+    const f32x2 t = add2(sum, y);
+    c = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
+// ---- mbarrier helpers of the row engine
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cnt(unsigned long long* bar, unsigned cnt) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(cnt)
+                 : "memory");
+}
+
+// Bounded wait that also gives up at once when the block has aborted.
+__device__ __forceinline__ bool mbar_wait_ab(unsigned long long* bar, unsigned parity,
+                                             unsigned long long timeout_ns, const volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (globaltimer() - t0 > timeout_ns) return false;
+    }
+    return true;
 }
 
 // Block-wide exclusive scan of the per-problem weights (m^2 for rows, m for
@@ -199,25 +269,12 @@ __device__ __forceinline__ void group_allreduce2(float& v0, float& v1, int gs, f
 
 struct SegCtx {
     const float* Gp;
-    int gs, m, ld, ng4, r_lo, r_hi, t, cur, nxt;
-    long long v0, TM;
-    float kap, fisa;
+    float4* rs_nxt;   // row scalars written by this sweep (problem-local)
+    float* flo_nxt;
+    const float4* rs_cur;   // row scalars of the previous iterate (problem-local)
+    int gs, m, ld, ng4, r_lo, r_hi, t, ng, nchunks;
+    float kap;
 };
-
-// Per-row scalars of the previous iteration, loaded one chunk ahead.
-struct RowScalars {
-    float F;    // row potential (hi part)
-    float al;   // a_i (unnormalised)
-    float rf;   // 2^lo of the row potential
-};
-
-__device__ __forceinline__ void load_scalars(RowScalars& R, const BatchArgs& A, const SegCtx& X, int row) {
-    if (row >= X.r_hi) return;
-    const long long gi = X.v0 + row;
-    R.F = X.t > 1 ? A.fhi[X.cur * X.TM + gi] : 0.f;
-    R.al = A.a[gi];
-    R.rf = X.t > 1 ? A.frf[X.cur * X.TM + gi] : 1.f;
-}
 
 // The staged column data of the current problem (shared memory): hi parts of
 // the column potentials and their lo factors (padding: -inf and 0).
@@ -226,22 +283,74 @@ struct ColData {
     const float4* cf;
 };
 
-__device__ __forceinline__ float4 exps4(const float4 c, const float4 gg, float kap, float F) {
-    return make_float4(ex2(fmaf(c.x, -kap, gg.x) + F), ex2(fmaf(c.y, -kap, gg.y) + F),
-                       ex2(fmaf(c.z, -kap, gg.z) + F), ex2(fmaf(c.w, -kap, gg.w) + F));
+// Exponentials of a float4 of costs around the potential F (log2 units):
+// 2^(gamma_j - kap c_j + F), two lanes per f32x2 instruction.
+__device__ __forceinline__ float4 exps4(const float4 c, const float4 gg, f32x2 nk2, f32x2 F2) {
+    const float2 x01 = upk(add2(fma2(pk(c.x, c.y), nk2, pk(gg.x, gg.y)), F2));
+    const float2 x23 = upk(add2(fma2(pk(c.z, c.w), nk2, pk(gg.z, gg.w)), F2));
+    return make_float4(ex2(x01.x), ex2(x01.y), ex2(x23.x), ex2(x23.y));
 }
 
-__device__ __forceinline__ float dot4(const float4 e, const float4 c, float s) {
-    return fmaf(e.x, c.x, fmaf(e.y, c.y, fmaf(e.z, c.z, fmaf(e.w, c.w, s))));
+// S += e . c on both lanes of a packed accumulator.
+__device__ __forceinline__ f32x2 dot4x2(const float4 e, const float4 c, f32x2 S) {
+    return fma2(pk(e.z, e.w), pk(c.z, c.w), fma2(pk(e.x, e.y), pk(c.x, c.y), S));
 }
 
-// Compensated (Kahan) addition: sum + c carries the running total of the added
-// values to about one rounding, however many rows a thread accumulates.
-__device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
-    const float y = __fsub_rn(v, c);
-    const float t = __fadd_rn(sum, y);
-    c = __fsub_rn(__fsub_rn(t, sum), y);
-    sum = t;
+__device__ __forceinline__ float hsum(f32x2 v) {
+    const float2 x = upk(v);
+    return x.x + x.y;
+}
+
+// Pipeline state of a block: chunks are numbered in the order the block
+// consumes them (across segments and sweeps); chunk n uses stage n % STAGES and
+// completes phase (n / STAGES) & 1 of that stage's full and empty barriers.
+// Every warp arrives once on a chunk's empty barrier when it no longer reads the
+// stage; thread 0 issues the copies.
+struct Pipe {
+    float* stage;                 // [STAGES][2 * OT_BATCH_MAXM]
+    float4* rsc;                  // [STAGES][2 * OT_BW] scalars of the chunk's rows
+    unsigned long long* full;     // [STAGES]
+    unsigned long long* empty;    // [STAGES] (OT_BW arrivals)
+    volatile int* abort;          // set by the first expired wait; later waits give up at once
+    long long consumed;           // chunks consumed so far (every thread)
+    long long issued;             // chunks issued so far (thread 0)
+};
+
+__device__ __forceinline__ void abort_block(const BatchArgs& A, const Pipe& P) {
+    if (!*P.abort) {
+        *P.abort = 1;
+        set_status(A.ctrl, OT_ERR_TIMEOUT);
+    }
+}
+
+// The warp no longer reads the current chunk's stage.
+template <int STAGES>
+__device__ __forceinline__ void stage_release(const Pipe& P) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive_cnt(&P.empty[P.consumed % STAGES], 1u);
+}
+
+// Chunk k of a segment (thread 0): rows r_lo + 2 k NG .. (2 NG consecutive rows,
+// two per group) and their scalars, two bulk copies (rows are contiguous with
+// stride ld; all sizes and addresses 16-byte multiples).  The stage is taken
+// once every warp has released the chunk that used it before.  (No proxy fence
+// before a refill: the stage was only read through the generic proxy, and the
+// release/acquire pair on the empty barrier orders those reads first.)
+template <int STAGES>
+__device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int k, const BatchArgs& A) {
+    const long long n = P.issued;
+    const int st = (int)(n % STAGES);
+    if (n >= STAGES && !mbar_wait_ab(&P.empty[st], (unsigned)(((n - STAGES) / STAGES) & 1), A.timeout_ns, P.abort))
+        abort_block(A, P);
+    if (*P.abort) return;
+    const int r0 = X.r_lo + 2 * k * X.ng;
+    const int nr = min(2 * X.ng, X.r_hi - r0);
+    const unsigned bytes = (unsigned)nr * (unsigned)X.ld * 4u, sbytes = (unsigned)nr * 16u;
+    unsigned long long* bar = &P.full[st];
+    mbar_arrive_expect_tx(bar, bytes + sbytes);
+    bulk_g2s(P.stage + (size_t)st * 2 * OT_BATCH_MAXM, X.Gp + (long long)r0 * X.ld, bytes, bar);
+    bulk_g2s(P.rsc + st * 2 * OT_BW, X.rs_cur + r0, sbytes, bar);
+    P.issued = n + 1;
 }
 
 // Row update of the two rows of a chunk held by a group (Eq.
@@ -249,86 +358,102 @@ __device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
 // around the previous potential F_r, new potential F_r - log2(S_r / alpha_r)
 // kept exactly as hi + lo, column contributions (alpha_r / S_r) e_rj added to
 // acc.  An explicit max shift is used on the first sweep and whenever a row
-// sum leaves the safe range.
-__device__ __forceinline__ void process_rows(const float* srow, const RowScalars (&R)[2], const BatchArgs& A,
+// sum leaves the safe range (then from the rows in global memory: the stage may
+// already be refilled).
+template <int STAGES>
+__device__ __forceinline__ void process_rows(const float* srow, const float4* srsc, const BatchArgs& A,
                                              const SegCtx& X, int row, int k, const ColData& CR, float* s_part,
-                                             int& parity, float4 (&acc)[OT_BV], float4 (&cmp)[OT_BV], float& l1) {
-    if (row >= X.r_hi) return;   // uniform over the group
+                                             int& parity, f32x2 (&acc)[2 * OT_BV], f32x2 (&cmp)[2 * OT_BV],
+                                             float& l1, Pipe& P) {
     const int GS = X.gs, gt = threadIdx.x & (GS - 1), nw = GS >> 5;
-    const bool two = row + 1 < X.r_hi;
+    const bool two = row + 1 < X.r_hi;   // uniform over the group
     // epilogue threads of the two rows: lane 0 of rotating warps (lanes 0 and 1 of a warp group)
     const int ep0 = GS > 32 ? (((2 * k) % nw) << 5) : 0;
     const int ep1 = GS > 32 ? (((2 * k + 1) % nw) << 5) : 1;
-    const float kap = X.kap;
-    const float al0 = R[0].al * X.fisa, al1 = R[1].al * X.fisa;
+    const float4 sc0 = srsc[0], sc1 = srsc[1];   // (the second is unused for a lone last row)
+    const float al0 = sc0.z, al1 = sc1.z;
+    const f32x2 nk2 = pk(-X.kap, -X.kap);
     const float4* c0 = reinterpret_cast<const float4*>(srow);
     const float4* c1 = reinterpret_cast<const float4*>(srow + X.ld);
     float4 e0[OT_BV], e1[OT_BV];
-    float F0 = R[0].F, F1 = R[1].F, S0 = 0.f, S1 = 0.f;
-    bool shifted = X.t == 1;
+    float F0 = sc0.x, F1 = sc1.x, S0 = 0.f, S1 = 0.f;
+    const bool first = X.t == 1;
+    bool shifted = first;
     if (!shifted) {
+        const f32x2 F02 = pk(F0, F0), F12 = pk(F1, F1);
+        f32x2 S02 = pk(0.f, 0.f), S12 = pk(0.f, 0.f);
 #pragma unroll
         for (int v = 0; v < OT_BV; ++v) {
             const int g = gt + v * GS;
             e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g < X.ng4) {
                 const float4 gg = CR.gc[g], cc = CR.cf[g];
-                e0[v] = exps4(c0[g], gg, kap, F0);
-                S0 = dot4(e0[v], cc, S0);
+                e0[v] = exps4(c0[g], gg, nk2, F02);
+                S02 = dot4x2(e0[v], cc, S02);
                 if (two) {
-                    e1[v] = exps4(c1[g], gg, kap, F1);
-                    S1 = dot4(e1[v], cc, S1);
+                    e1[v] = exps4(c1[g], gg, nk2, F12);
+                    S12 = dot4x2(e1[v], cc, S12);
                 }
             }
         }
+        stage_release<STAGES>(P);
+        S0 = hsum(S02);
+        S1 = hsum(S12);
         group_allreduce2<false>(S0, S1, GS, s_part, parity);
-        if (gt == ep0) l1 += fabsf(fmaf(S0, R[0].rf - 1.0f, S0 - al0));
-        if (two && gt == ep1) l1 += fabsf(fmaf(S1, R[1].rf - 1.0f, S1 - al1));
+        if (threadIdx.x == 0 && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
+        if (gt == ep0) l1 += fabsf(fmaf(S0, sc0.y - 1.0f, S0 - al0));
+        if (two && gt == ep1) l1 += fabsf(fmaf(S1, sc1.y - 1.0f, S1 - al1));
         // uniform over the group
         shifted = !(S0 > 1e-30f && S0 < 1e30f) || (two && !(S1 > 1e-30f && S1 < 1e30f));
     }
     if (shifted) {
         // explicit shifts F_r = -max_j (gamma_j - kap c_rj), both rows
+        const float4* r0 = first ? c0 : reinterpret_cast<const float4*>(X.Gp + (long long)row * X.ld);
+        const float4* r1 = first ? c1 : reinterpret_cast<const float4*>(X.Gp + (long long)(row + 1) * X.ld);
         float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
         for (int v = 0; v < OT_BV; ++v) {
             const int g = gt + v * GS;
-            e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            e0[v] = e1[v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
             if (g < X.ng4) {
                 const float4 gg = CR.gc[g];
-                float4 c = c0[g];
-                e0[v] = make_float4(fmaf(c.x, -kap, gg.x), fmaf(c.y, -kap, gg.y), fmaf(c.z, -kap, gg.z),
-                                    fmaf(c.w, -kap, gg.w));
-                m0 = fmaxf(m0, fmaxf(fmaxf(e0[v].x, e0[v].y), fmaxf(e0[v].z, e0[v].w)));
+                float4 c = r0[g];
+                float2 x01 = upk(fma2(pk(c.x, c.y), nk2, pk(gg.x, gg.y)));
+                float2 x23 = upk(fma2(pk(c.z, c.w), nk2, pk(gg.z, gg.w)));
+                e0[v] = make_float4(x01.x, x01.y, x23.x, x23.y);
+                m0 = fmaxf(m0, fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y)));
                 if (two) {
-                    c = c1[g];
-                    e1[v] = make_float4(fmaf(c.x, -kap, gg.x), fmaf(c.y, -kap, gg.y), fmaf(c.z, -kap, gg.z),
-                                        fmaf(c.w, -kap, gg.w));
-                    m1 = fmaxf(m1, fmaxf(fmaxf(e1[v].x, e1[v].y), fmaxf(e1[v].z, e1[v].w)));
+                    c = r1[g];
+                    x01 = upk(fma2(pk(c.x, c.y), nk2, pk(gg.x, gg.y)));
+                    x23 = upk(fma2(pk(c.z, c.w), nk2, pk(gg.z, gg.w)));
+                    e1[v] = make_float4(x01.x, x01.y, x23.x, x23.y);
+                    m1 = fmaxf(m1, fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y)));
                 }
             }
         }
+        if (first) stage_release<STAGES>(P);
         group_allreduce2<true>(m0, m1, GS, s_part, parity);
+        if (first && threadIdx.x == 0 && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
         F0 = m0 > -INFINITY ? -m0 : 0.f;
         F1 = m1 > -INFINITY ? -m1 : 0.f;
-        S0 = S1 = 0.f;
+        f32x2 S02 = pk(0.f, 0.f), S12 = pk(0.f, 0.f);
 #pragma unroll
         for (int v = 0; v < OT_BV; ++v) {
             const int g = gt + v * GS;
+            float4 x = e0[v];
+            x = make_float4(ex2(x.x + F0), ex2(x.y + F0), ex2(x.z + F0), ex2(x.w + F0));
+            e0[v] = x;
+            x = e1[v];
+            x = make_float4(ex2(x.x + F1), ex2(x.y + F1), ex2(x.z + F1), ex2(x.w + F1));
+            e1[v] = x;
             if (g < X.ng4) {
-                float4 x = e0[v];
-                x = make_float4(ex2(x.x + F0), ex2(x.y + F0), ex2(x.z + F0), ex2(x.w + F0));
-                e0[v] = x;
                 const float4 cc = CR.cf[g];
-                S0 = dot4(x, cc, S0);
-                if (two) {
-                    x = e1[v];
-                    x = make_float4(ex2(x.x + F1), ex2(x.y + F1), ex2(x.z + F1), ex2(x.w + F1));
-                    e1[v] = x;
-                    S1 = dot4(x, cc, S1);
-                }
+                S02 = dot4x2(e0[v], cc, S02);
+                S12 = dot4x2(e1[v], cc, S12);
             }
         }
+        S0 = hsum(S02);
+        S1 = hsum(S12);
         group_allreduce2<false>(S0, S1, GS, s_part, parity);
     }
     float u0 = 0.f, u1 = 0.f;
@@ -342,136 +467,84 @@ __device__ __forceinline__ void process_rows(const float* srow, const RowScalars
             else u0 = __fdividef(al, S);
             if (gt == ep) {
                 // new potential F - log2(S / alpha) held exactly as hi + lo (TwoSum)
-                const long long gi = X.v0 + row + r;
                 const float b = -lg2(__fdividef(S, al));
                 const float hi = __fadd_rn(F, b);
                 const float bv = __fsub_rn(hi, F);
                 const float lo = __fadd_rn(__fsub_rn(F, __fsub_rn(hi, bv)), __fsub_rn(b, bv));
-                A.fhi[X.nxt * X.TM + gi] = hi;
-                A.flo[X.nxt * X.TM + gi] = lo;
-                A.frf[X.nxt * X.TM + gi] = ex2(lo);
+                X.rs_nxt[row + r] = make_float4(hi, ex2(lo), al, 0.f);
+                X.flo_nxt[row + r] = lo;
             }
         } else if (gt == ep) {
             set_status(A.ctrl, OT_ERR_NONFINITE);
         }
     }
+    const f32x2 u02 = pk(u0, u0), u12 = pk(u1, u1);
 #pragma unroll
     for (int v = 0; v < OT_BV; ++v) {
-        kahan_add(acc[v].x, cmp[v].x, fmaf(u1, e1[v].x, u0 * e0[v].x));
-        kahan_add(acc[v].y, cmp[v].y, fmaf(u1, e1[v].y, u0 * e0[v].y));
-        kahan_add(acc[v].z, cmp[v].z, fmaf(u1, e1[v].z, u0 * e0[v].z));
-        kahan_add(acc[v].w, cmp[v].w, fmaf(u1, e1[v].w, u0 * e0[v].w));
+        kahan2(acc[2 * v], cmp[2 * v], fma2(u12, pk(e1[v].x, e1[v].y), mul2(u02, pk(e0[v].x, e0[v].y))));
+        kahan2(acc[2 * v + 1], cmp[2 * v + 1], fma2(u12, pk(e1[v].z, e1[v].w), mul2(u02, pk(e0[v].z, e0[v].w))));
     }
-}
-
-// Pipeline state of a block: chunks are numbered in the order the block
-// consumes them (across segments and sweeps); chunk n uses stage n % STAGES
-// and completes phase (n / STAGES) & 1 of that stage's barrier.
-struct Pipe {
-    float* stage;                 // [STAGES][2 * OT_BATCH_MAXM]
-    unsigned long long* full;     // [STAGES]
-    long long consumed;           // chunks consumed so far
-    long long issued;             // chunks issued so far
-};
-
-// Chunk k of a segment: rows r_lo + 2 k NG .. (2 NG consecutive rows, two per
-// group), one bulk copy (rows are contiguous with stride ld; 16-byte multiples).
-template <int STAGES>
-__device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int NG, int k) {
-    const int r0 = X.r_lo + 2 * k * NG;
-    const int nr = min(2 * NG, X.r_hi - r0);
-    const unsigned bytes = (unsigned)nr * (unsigned)X.ld * 4u;
-    const int st = (int)(P.issued % STAGES);
-    unsigned long long* bar = &P.full[st];
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(P.stage + (size_t)st * 2 * OT_BATCH_MAXM, X.Gp + (long long)r0 * X.ld, bytes, bar);
-    P.issued += 1;
 }
 
 // Rows [r_lo, r_hi) of one problem by all groups of the block.  Chunk k holds
 // rows r_lo + 2 (k NG + q) and the next one for group q; STAGES chunks are in
-// flight.  Returns false (uniformly) if a copy did not complete in time.
+// flight.  Returns false (uniformly) if a wait expired.
 template <int STAGES>
 __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p, int r_lo, int r_hi, int t,
-                             int GS, float* s_part, float* s_gc, float* s_cf, double isa, Pipe& P) {
+                             int GS, float* s_part, float* s_gc, float* s_cf, Pipe& P) {
     const int NG = OT_BT / GS;
     const int tid = threadIdx.x, gt = tid & (GS - 1), q = tid / GS;
+    const int cur = (t - 1) & 1, nxt = t & 1;
     SegCtx X;
     X.Gp = A.G + d.g_off;
+    X.rs_cur = A.rs + (size_t)cur * A.total_m + d.v_off;
+    X.rs_nxt = A.rs + (size_t)nxt * A.total_m + d.v_off;
+    X.flo_nxt = A.flo + (size_t)nxt * A.total_m + d.v_off;
     X.gs = GS;
+    X.ng = NG;
     X.m = d.m;
     X.ld = d.ld;
     X.ng4 = d.ld >> 2;
     X.r_lo = r_lo;
     X.r_hi = r_hi;
     X.t = t;
-    X.cur = (t - 1) & 1;
-    X.nxt = X.cur ^ 1;
-    X.v0 = d.v_off;
-    X.TM = A.total_m;
     X.kap = (float)(1.0 / ((double)d.eps * OT_LN2));
-    X.fisa = (float)isa;
-    const int nchunks = (r_hi - r_lo + 2 * NG - 1) / (2 * NG);
-    // (no proxy fence before a refill: a stage's previous contents were only read
-    // through the generic proxy, and a block barrier orders those reads first)
+    X.nchunks = (r_hi - r_lo + 2 * NG - 1) / (2 * NG);
     if (tid == 0) {
-        for (int k = 0; k < nchunks && k < STAGES; ++k) issue_chunk<STAGES>(P, X, NG, k);
+        for (int k = 0; k < X.nchunks && k < STAGES; ++k) issue_chunk<STAGES>(P, X, k, A);
     }
-    long long issued = P.consumed + min(nchunks, STAGES);   // block-uniform copy of P.issued
     // stage the column data (every thread has finished with the previous segment's)
     __syncthreads();
     for (int j = tid; j < X.ld; j += OT_BT) {
         const bool in = j < X.m;
-        s_gc[j] = in ? A.gc[X.v0 + j] : -INFINITY;
-        s_cf[j] = in ? A.cf[X.v0 + j] : 0.f;
+        s_gc[j] = in ? A.gc[d.v_off + j] : -INFINITY;
+        s_cf[j] = in ? A.cf[d.v_off + j] : 0.f;
     }
     __syncthreads();
     ColData CR;
     CR.gc = reinterpret_cast<const float4*>(s_gc);
     CR.cf = reinterpret_cast<const float4*>(s_cf);
     int parity = 0;
-    float4 acc[OT_BV], cmp[OT_BV];   // column contributions (compensated sums)
+    f32x2 acc[2 * OT_BV], cmp[2 * OT_BV];   // column contributions (compensated sums)
 #pragma unroll
-    for (int v = 0; v < OT_BV; ++v) acc[v] = cmp[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int v = 0; v < 2 * OT_BV; ++v) acc[v] = cmp[v] = pk(0.f, 0.f);
     float l1 = 0.f;
-    RowScalars cur[2], nxt[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        cur[r].F = nxt[r].F = 0.f;
-        cur[r].al = nxt[r].al = 1.f;
-        cur[r].rf = nxt[r].rf = 1.f;
-        load_scalars(cur[r], A, X, r_lo + 2 * q + r);
-    }
-    bool ok = true;
-    for (int k = 0; k < nchunks; ++k) {
+    for (int k = 0; k < X.nchunks; ++k) {
         const int row = r_lo + 2 * (k * NG + q);
-        if (k + 1 < nchunks) {
-            load_scalars(nxt[0], A, X, row + 2 * NG);
-            load_scalars(nxt[1], A, X, row + 2 * NG + 1);
-        }
         const int st = (int)(P.consumed % STAGES);
         const unsigned ph = (unsigned)((P.consumed / STAGES) & 1);
-        const bool got = mbar_wait(&P.full[st], ph, A.timeout_ns);
-        // processed even after an expired wait (shared-memory reads stay in bounds), so
-        // that every thread of a group meets the group's barriers; the block then
-        // leaves together on the decision below
-        process_rows(P.stage + (size_t)st * 2 * OT_BATCH_MAXM + (size_t)(2 * q) * X.ld, cur, A, X, row, k, CR,
-                     s_part, parity, acc, cmp, l1);
-        // every thread has read the stage (its exponentials are in registers): refill it
-        if (__syncthreads_or(!got)) {
-            ok = false;
-            break;
-        }
+        if (!mbar_wait_ab(&P.full[st], ph, A.timeout_ns, P.abort)) abort_block(A, P);
+        // (processed even after an expired wait: the shared-memory reads stay in bounds, and
+        // every warp keeps to the same sequence of group barriers and releases; the block
+        // leaves together at the end of the segment)
+        if (row < r_hi)   // uniform over the group
+            process_rows<STAGES>(P.stage + (size_t)st * 2 * OT_BATCH_MAXM + (size_t)(2 * q) * X.ld,
+                                 P.rsc + st * 2 * OT_BW + 2 * q, A, X, row, k, CR, s_part, parity, acc, cmp, l1, P);
+        else
+            stage_release<STAGES>(P);
         P.consumed += 1;
-        if (k + STAGES < nchunks) {
-            if (tid == 0) issue_chunk<STAGES>(P, X, NG, k + STAGES);
-            issued += 1;
-        }
-        cur[0] = nxt[0];
-        cur[1] = nxt[1];
     }
-    P.issued = issued;
-    if (!ok) return false;
+    if (__syncthreads_or(*P.abort)) return false;
     // column contributions of this group (times the lo factors) and its L1 terms
     if (r_lo + 2 * q < r_hi) {
 #pragma unroll
@@ -479,12 +552,14 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
             const int g = gt + v * GS;
             if (g < X.ng4) {
                 const float4 cc = CR.cf[g];
+                const float2 s01 = upk(sub2(acc[2 * v], cmp[2 * v]));
+                const float2 s23 = upk(sub2(acc[2 * v + 1], cmp[2 * v + 1]));
                 const int j = 4 * g;
-                const long long o = X.v0 + j;
-                if (j < X.m) red_add_f32(A.R + o, (acc[v].x - cmp[v].x) * cc.x);
-                if (j + 1 < X.m) red_add_f32(A.R + o + 1, (acc[v].y - cmp[v].y) * cc.y);
-                if (j + 2 < X.m) red_add_f32(A.R + o + 2, (acc[v].z - cmp[v].z) * cc.z);
-                if (j + 3 < X.m) red_add_f32(A.R + o + 3, (acc[v].w - cmp[v].w) * cc.w);
+                const long long o = d.v_off + j;
+                if (j < X.m) red_add_f32(A.R + o, s01.x * cc.x);
+                if (j + 1 < X.m) red_add_f32(A.R + o + 1, s01.y * cc.y);
+                if (j + 2 < X.m) red_add_f32(A.R + o + 2, s23.x * cc.z);
+                if (j + 3 < X.m) red_add_f32(A.R + o + 3, s23.y * cc.w);
             }
         }
     }
@@ -504,7 +579,8 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
     __shared__ float s_part[2 * OT_BW * 2];
     __shared__ long long s_wsum[32];
     __shared__ double s_dred[OT_BW];
-    __shared__ unsigned long long s_full[STAGES];
+    __shared__ __align__(8) unsigned long long s_full[STAGES], s_empty[STAGES];
+    __shared__ int s_abort;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int B = blockIdx.x, Gd = gridDim.x;
@@ -512,12 +588,19 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
     unsigned epoch = 0;
     Pipe P;
     P.stage = s_stage;
+    P.rsc = reinterpret_cast<float4*>(dsm + BatchSmem::rsc);
     P.full = s_full;
+    P.empty = s_empty;
+    P.abort = &s_abort;
     P.consumed = 0;
     P.issued = 0;
 
     if (tid == 0) {
-        for (int st = 0; st < STAGES; ++st) mbar_init(&s_full[st], 1);
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&s_full[st], 1);
+            mbar_init(&s_empty[st], OT_BW);
+        }
+        s_abort = 0;
         fence_mbar_init();
     }
     for (int p = tid; p < count; p += OT_BT) s_m[p] = A.desc[p].m;
@@ -567,6 +650,15 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 A.res[p].marg_l2_col = -1.0;
             }
         }
+        // row scalars of both buffers (no potential yet: the first sweep shifts every row)
+        const double isa = 1.0 / ta;
+        for (int i = tid; i < m; i += OT_BT) {
+            const float4 r0 = make_float4(0.f, 1.f, (float)((double)A.a[v0 + i] * isa), 0.f);
+            A.rs[v0 + i] = r0;
+            A.rs[A.total_m + v0 + i] = r0;
+            A.flo[v0 + i] = 0.f;
+            A.flo[A.total_m + v0 + i] = 0.f;
+        }
         // column potentials and sums
         const float kap = (float)(1.0 / ((double)d.eps * OT_LN2));
         for (int j = tid; j < m; j += OT_BT) {
@@ -601,15 +693,11 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 if (r_lo >= r_hi) continue;
                 const ot_problem_desc d = A.desc[p];
                 const int ld = d.ld;
-                const double isa = A.inv_sa[p];
                 // group size: the smallest power of two >= 32 whose OT_BV float4 slots cover the row
                 int gs = 32;
                 while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
                 gs = min(OT_BT, gs << A.gs_shift);   // tuned: a larger group takes fewer slots per thread
-                if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, isa, P)) {
-                    if (tid == 0) set_status(A.ctrl, OT_ERR_TIMEOUT);
-                    goto fail;
-                }
+                if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, P)) goto fail;
             }
         }
         if (!grid_sync(A.ctrl, Gd, A.timeout_ns, epoch)) goto fail;
@@ -662,8 +750,9 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                     const float* Gp = A.G + d.g_off;
                     float mx = -INFINITY, s = 0.f;
                     for (int i = 0; i < m; ++i) {
-                        const float x = fmaf(Gp[(long long)i * ld + j], -kap, A.fhi[nxt * TM + v0 + i]);
-                        const float e = A.frf[nxt * TM + v0 + i];
+                        const float4 ri = A.rs[nxt * TM + v0 + i];
+                        const float x = fmaf(Gp[(long long)i * ld + j], -kap, ri.x);
+                        const float e = ri.y;
                         if (x > mx) { s = fmaf(s, ex2(mx - x), e); mx = x; }
                         else s += ex2(x - mx) * e;
                     }
@@ -697,16 +786,17 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         for (int i = tid; i < m; i += OT_BT) {
             // a problem rejected by the validation gets NaN potentials
             const size_t o = (size_t)buf * A.total_m + v0 + i;
-            A.w_out[v0 + i] = it < 0 ? (double)NAN : ((double)A.fhi[o] + (double)A.flo[o]) * unit + shift;
+            A.w_out[v0 + i] = it < 0 ? (double)NAN : ((double)A.rs[o].x + (double)A.flo[o]) * unit + shift;
             A.z_out[v0 + i] = it < 0 ? (double)NAN : A.gam[v0 + i] * unit;
         }
         if (tid == 0) A.res[p].reserved[1] = 4.0;   // variant code: batch
     }
     return;
 fail:
-    // no copy may still be writing into this block's shared memory when it exits
+    // no copy may still be writing into this block's shared memory when it exits (once the
+    // block aborted no copy is issued, and at most the last STAGES issued can be in flight)
     if (tid == 0) {
-        for (long long u = P.consumed; u < P.issued; ++u)
+        for (long long u = P.issued > STAGES ? P.issued - STAGES : 0; u < P.issued; ++u)
             if (!mbar_wait(&s_full[u % STAGES], (unsigned)((u / STAGES) & 1), A.timeout_ns)) break;
         for (int p = B; p < count; p += Gd) {
             A.res[p].iters = -1;
@@ -771,7 +861,7 @@ __global__ void batch_single_table_kernel(ot_problem_desc d, ot_problem_desc* ds
 }
 
 struct BatchLayout {
-    size_t ctrl, desc, inv_sa, inv_sb, active, iters, l1acc, flo, fhi, frf, gam, gc, cf, R, total;
+    size_t ctrl, desc, inv_sa, inv_sb, active, iters, l1acc, rs, flo, gam, gc, cf, R, total;
 };
 
 static BatchLayout batch_layout(int count, long long TM) {
@@ -784,9 +874,8 @@ static BatchLayout batch_layout(int count, long long TM) {
     L.active = o; o = a256(o + sizeof(int) * (size_t)count);
     L.iters = o; o = a256(o + sizeof(int) * (size_t)count);
     L.l1acc = o; o = a256(o + sizeof(double) * 2 * (size_t)count);
+    L.rs = o; o = a256(o + sizeof(float4) * 2 * (size_t)TM);
     L.flo = o; o = a256(o + sizeof(float) * 2 * (size_t)TM);
-    L.fhi = o; o = a256(o + sizeof(float) * 2 * (size_t)TM);
-    L.frf = o; o = a256(o + sizeof(float) * 2 * (size_t)TM);
     L.gam = o; o = a256(o + sizeof(double) * (size_t)TM);
     L.gc = o; o = a256(o + sizeof(float) * (size_t)TM);
     L.cf = o; o = a256(o + sizeof(float) * (size_t)TM);
@@ -940,9 +1029,8 @@ static int batch_solve_cfg(int count, long long total_m, const float* G_all, con
     A.active = (int*)(base + L.active);
     A.iters = (int*)(base + L.iters);
     A.l1acc = (double*)(base + L.l1acc);
+    A.rs = (float4*)(base + L.rs);
     A.flo = (float*)(base + L.flo);
-    A.fhi = (float*)(base + L.fhi);
-    A.frf = (float*)(base + L.frf);
     A.gam = (double*)(base + L.gam);
     A.gc = (float*)(base + L.gc);
     A.cf = (float*)(base + L.cf);
