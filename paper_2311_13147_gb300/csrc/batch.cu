@@ -353,23 +353,47 @@ __device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int k, con
     P.issued = n + 1;
 }
 
+// A row whose new potential is still to be written: lane i of a group's first
+// warp holds the rows with chunk-local index i mod 32 (two per chunk), and that
+// warp writes 32 of them at once (no serial chain of special functions on one
+// lane per chunk).
+struct Pending {
+    float S, F, al;
+    int row;   // -1: none
+};
+
+// New potential F - log2(S / alpha) of a pending row, held exactly as hi + lo (TwoSum).
+__device__ __forceinline__ void finish_pending(const BatchArgs& A, const SegCtx& X, Pending& pd) {
+    if (pd.row < 0) return;
+    if (pd.S > 1e-30f && pd.S < 1e30f) {
+        const float b = -lg2(__fdividef(pd.S, pd.al));
+        const float hi = __fadd_rn(pd.F, b);
+        const float bv = __fsub_rn(hi, pd.F);
+        const float lo = __fadd_rn(__fsub_rn(pd.F, __fsub_rn(hi, bv)), __fsub_rn(b, bv));
+        X.rs_nxt[pd.row] = make_float4(hi, ex2(lo), pd.al, 0.f);
+        X.flo_nxt[pd.row] = lo;
+    } else {
+        set_status(A.ctrl, OT_ERR_NONFINITE);
+    }
+    pd.row = -1;
+}
+
 // Row update of the two rows of a chunk held by a group (Eq.
 // optimal_f_sinkhorn_logdomain in log2 units): S_r = sum_j 2^(gamma_j - kap c_rj + F_r)
 // around the previous potential F_r, new potential F_r - log2(S_r / alpha_r)
-// kept exactly as hi + lo, column contributions (alpha_r / S_r) e_rj added to
-// acc.  An explicit max shift is used on the first sweep and whenever a row
+// kept exactly as hi + lo (recorded in pd, written by finish_pending), column
+// contributions (alpha_r / S_r) e_rj added to acc.  An explicit max shift is used on the first sweep and whenever a row
 // sum leaves the safe range (then from the rows in global memory: the stage may
 // already be refilled).
 template <int STAGES>
 __device__ __forceinline__ void process_rows(const float* srow, const float4* srsc, const BatchArgs& A,
                                              const SegCtx& X, int row, int k, const ColData& CR, float* s_part,
                                              int& parity, f32x2 (&acc)[2 * OT_BV], f32x2 (&cmp)[2 * OT_BV],
-                                             float& l1, Pipe& P) {
-    const int GS = X.gs, gt = threadIdx.x & (GS - 1), nw = GS >> 5;
+                                             float& l1, Pending& pd, Pipe& P) {
+    const int GS = X.gs, gt = threadIdx.x & (GS - 1);
     const bool two = row + 1 < X.r_hi;   // uniform over the group
-    // epilogue threads of the two rows: lane 0 of rotating warps (lanes 0 and 1 of a warp group)
-    const int ep0 = GS > 32 ? (((2 * k) % nw) << 5) : 0;
-    const int ep1 = GS > 32 ? (((2 * k + 1) % nw) << 5) : 1;
+    // lanes of the group's first warp that hold the two rows until they are finished
+    const int ep0 = (2 * k) & 31, ep1 = ep0 + 1;
     const float4 sc0 = srsc[0], sc1 = srsc[1];   // (the second is unused for a lone last row)
     const float al0 = sc0.z, al1 = sc1.z;
     const f32x2 nk2 = pk(-X.kap, -X.kap);
@@ -456,28 +480,20 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
         S1 = hsum(S12);
         group_allreduce2<false>(S0, S1, GS, s_part, parity);
     }
-    float u0 = 0.f, u1 = 0.f;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const float S = r ? S1 : S0, F = r ? F1 : F0, al = r ? al1 : al0;
-        const int ep = r ? ep1 : ep0;
-        if (r == 1 && !two) break;
-        if (S > 1e-30f && S < 1e30f) {
-            if (r) u1 = __fdividef(al, S);
-            else u0 = __fdividef(al, S);
-            if (gt == ep) {
-                // new potential F - log2(S / alpha) held exactly as hi + lo (TwoSum)
-                const float b = -lg2(__fdividef(S, al));
-                const float hi = __fadd_rn(F, b);
-                const float bv = __fsub_rn(hi, F);
-                const float lo = __fadd_rn(__fsub_rn(F, __fsub_rn(hi, bv)), __fsub_rn(b, bv));
-                X.rs_nxt[row + r] = make_float4(hi, ex2(lo), al, 0.f);
-                X.flo_nxt[row + r] = lo;
-            }
-        } else if (gt == ep) {
-            set_status(A.ctrl, OT_ERR_NONFINITE);
-        }
+    if (gt == ep0) {
+        pd.S = S0;
+        pd.F = F0;
+        pd.al = al0;
+        pd.row = row;
     }
+    if (two && gt == ep1) {
+        pd.S = S1;
+        pd.F = F1;
+        pd.al = al1;
+        pd.row = row + 1;
+    }
+    const float u0 = (S0 > 1e-30f && S0 < 1e30f) ? __fdividef(al0, S0) : 0.f;
+    const float u1 = (two && S1 > 1e-30f && S1 < 1e30f) ? __fdividef(al1, S1) : 0.f;
     const f32x2 u02 = pk(u0, u0), u12 = pk(u1, u1);
 #pragma unroll
     for (int v = 0; v < OT_BV; ++v) {
@@ -529,6 +545,9 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
 #pragma unroll
     for (int v = 0; v < 2 * OT_BV; ++v) acc[v] = cmp[v] = pk(0.f, 0.f);
     float l1 = 0.f;
+    Pending pd;
+    pd.S = pd.F = pd.al = 0.f;
+    pd.row = -1;
     for (int k = 0; k < X.nchunks; ++k) {
         const int row = r_lo + 2 * (k * NG + q);
         const int st = (int)(P.consumed % STAGES);
@@ -539,9 +558,12 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
         // leaves together at the end of the segment)
         if (row < r_hi)   // uniform over the group
             process_rows<STAGES>(P.stage + (size_t)st * 2 * OT_BATCH_MAXM + (size_t)(2 * q) * X.ld,
-                                 P.rsc + st * 2 * OT_BW + 2 * q, A, X, row, k, CR, s_part, parity, acc, cmp, l1, P);
+                                 P.rsc + st * 2 * OT_BW + 2 * q, A, X, row, k, CR, s_part, parity, acc, cmp, l1, pd,
+                                 P);
         else
             stage_release<STAGES>(P);
+        // the group's first warp writes its 32 pending rows every 16 chunks and at the end
+        if (gt < 32 && ((k & 15) == 15 || k == X.nchunks - 1)) finish_pending(A, X, pd);
         P.consumed += 1;
     }
     if (__syncthreads_or(*P.abort)) return false;
@@ -676,6 +698,8 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         const int nxt = t & 1;
         const long long TM = A.total_m;
         // ---------------- row phase
+        // (the row scalars written last sweep by generic stores are read by bulk copies)
+        if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (int p = tid; p < count; p += OT_BT) s_act[p] = A.active[p];
         __syncthreads();
         batch_prefix(count, s_m, s_act, true, s_pref, s_wsum);
@@ -700,6 +724,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, P)) goto fail;
             }
         }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         if (!grid_sync(A.ctrl, Gd, A.timeout_ns, epoch)) goto fail;
 
         // ---------------- column phase
