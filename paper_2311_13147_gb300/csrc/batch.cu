@@ -48,6 +48,9 @@ int device_sms();
 #define OT_BW (OT_BT / 32)
 #define OT_BV 4               // float4 column slots per thread and row
 #define OT_STAGES_MAX 2       // chunks in flight per block (bulk copies into shared memory)
+#ifndef OT_ROW_FIXED
+#define OT_ROW_FIXED 8        // per-chunk cost of a group that does not scale with its slots, in slots
+#endif
 #define OT_BATCH_NCFG 6       // tunable launch configurations (see decode_cfg)
 
 struct BatchArgs {
@@ -94,7 +97,8 @@ struct BatchSmem {
     static constexpr size_t pref = a128(cf + sizeof(float) * OT_BATCH_MAXM);
     static constexpr size_t msz = a128(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
     static constexpr size_t act = a128(msz + sizeof(int) * OT_BATCH_MAX);
-    static constexpr size_t total = a128(act + sizeof(int) * OT_BATCH_MAX);
+    static constexpr size_t rw = a128(act + sizeof(int) * OT_BATCH_MAX);
+    static constexpr size_t total = a128(rw + sizeof(int) * OT_BATCH_MAX);
 };
 static_assert(4 * OT_BV * OT_BT == OT_BATCH_MAXM, "a full block covers the longest row");
 static_assert(BatchSmem::total + 2048 <= 227 * 1024, "shared memory");
@@ -167,9 +171,29 @@ __device__ __forceinline__ bool mbar_wait_ab(unsigned long long* bar, unsigned p
     return true;
 }
 
-// Block-wide exclusive scan of the per-problem weights (m^2 for rows, m for
-// columns; 0 for finished problems) into s_pref[0..count].
-__device__ void batch_prefix(int count, const int* s_m, const int* act, bool rows, long long* s_pref,
+// Thread-group size of a problem's rows: the smallest power of two >= 32 whose
+// OT_BV float4 slots per thread cover the row stride (one size larger per shift).
+__host__ __device__ __forceinline__ int group_size(int ld, int shift) {
+    int gs = 32;
+    while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
+    gs <<= shift;
+    return gs < OT_BT ? gs : OT_BT;
+}
+
+// Estimated cost of one row of a problem, the unit of the row phase's work split:
+// a chunk costs its groups a fixed part plus a part per filled float4 slot, and
+// holds two rows per group, so a row costs GS (OT_ROW_FIXED + slots) / 2 thread
+// slots (the factor 1/2 is common to all problems and dropped).  Splitting by bytes
+// instead would give blocks with short rows more chunks than the others.
+__host__ __device__ __forceinline__ int row_weight(int ld, int shift) {
+    const int gs = group_size(ld, shift);
+    const int slots = (ld + 4 * gs - 1) / (4 * gs);
+    return gs * (OT_ROW_FIXED + slots);
+}
+
+// Block-wide exclusive scan of the per-problem weights (m x row weight for rows,
+// m for columns; 0 for finished problems) into s_pref[0..count].
+__device__ void batch_prefix(int count, const int* s_m, const int* s_rw, const int* act, bool rows, long long* s_pref,
                              long long* s_wsum) {
     // each thread sums a contiguous chunk, then a warp scan of the chunk sums
     const int tid = threadIdx.x;
@@ -178,7 +202,7 @@ __device__ void batch_prefix(int count, const int* s_m, const int* act, bool row
     long long loc = 0;
     for (int p = p0; p < p1; ++p) {
         const long long m = s_m[p];
-        loc += act[p] ? (rows ? m * m : m) : 0;
+        loc += act[p] ? (rows ? m * s_rw[p] : m) : 0;
     }
     const int lane = tid & 31, wid = tid >> 5;
     long long v = loc;
@@ -203,7 +227,7 @@ __device__ void batch_prefix(int count, const int* s_m, const int* act, bool row
     for (int p = p0; p < p1; ++p) {
         s_pref[p] = base;
         const long long m = s_m[p];
-        base += act[p] ? (rows ? m * m : m) : 0;
+        base += act[p] ? (rows ? m * s_rw[p] : m) : 0;
     }
     if (tid == OT_BT - 1) s_pref[count] = base;
     __syncthreads();
@@ -598,6 +622,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
     long long* s_pref = reinterpret_cast<long long*>(dsm + BatchSmem::pref);           // [count+1]
     int* s_m = reinterpret_cast<int*>(dsm + BatchSmem::msz);                           // [count]
     int* s_act = reinterpret_cast<int*>(dsm + BatchSmem::act);                         // [count]
+    int* s_rw = reinterpret_cast<int*>(dsm + BatchSmem::rw);                           // [count]
     __shared__ float s_part[2 * OT_BW * 2];
     __shared__ long long s_wsum[32];
     __shared__ double s_dred[OT_BW];
@@ -625,7 +650,10 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         s_abort = 0;
         fence_mbar_init();
     }
-    for (int p = tid; p < count; p += OT_BT) s_m[p] = A.desc[p].m;
+    for (int p = tid; p < count; p += OT_BT) {
+        s_m[p] = A.desc[p].m;
+        s_rw[p] = row_weight(A.desc[p].ld, A.gs_shift);
+    }
     __syncthreads();
 
     // ---- per-problem marginal sums and validation (problems split over blocks)
@@ -702,25 +730,21 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (int p = tid; p < count; p += OT_BT) s_act[p] = A.active[p];
         __syncthreads();
-        batch_prefix(count, s_m, s_act, true, s_pref, s_wsum);
+        batch_prefix(count, s_m, s_rw, s_act, true, s_pref, s_wsum);
         {
-            // a row belongs to the block whose weight range holds the row's first entry
+            // a row belongs to the block whose weight range holds the row's start
             const long long W = s_pref[count];
             const long long w0 = W * B / Gd, w1 = W * (B + 1) / Gd;
             const int pfirst = (W > 0 && w0 < w1) ? find_problem(s_pref, count, w0) : count;
             for (int p = pfirst; p < count && s_pref[p] < w1; ++p) {
                 if (!s_act[p]) continue;
-                const int m = s_m[p];
+                const int m = s_m[p], rw = s_rw[p];
                 const long long base = s_pref[p];
-                const int r_lo = (w0 <= base) ? 0 : (int)((w0 - base + m - 1) / m);
-                const int r_hi = min(m, (int)((w1 - base + m - 1) / m));
+                const int r_lo = (w0 <= base) ? 0 : (int)((w0 - base + rw - 1) / rw);
+                const int r_hi = min(m, (int)((w1 - base + rw - 1) / rw));
                 if (r_lo >= r_hi) continue;
                 const ot_problem_desc d = A.desc[p];
-                const int ld = d.ld;
-                // group size: the smallest power of two >= 32 whose OT_BV float4 slots cover the row
-                int gs = 32;
-                while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
-                gs = min(OT_BT, gs << A.gs_shift);   // tuned: a larger group takes fewer slots per thread
+                const int gs = group_size(d.ld, A.gs_shift);   // tuned: a larger group takes fewer slots per thread
                 if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, P)) goto fail;
             }
         }
@@ -728,7 +752,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         if (!grid_sync(A.ctrl, Gd, A.timeout_ns, epoch)) goto fail;
 
         // ---------------- column phase
-        batch_prefix(count, s_m, s_act, false, s_pref, s_wsum);
+        batch_prefix(count, s_m, s_rw, s_act, false, s_pref, s_wsum);
         {
             const long long W = s_pref[count];
             const long long c0 = W * B / Gd, c1 = W * (B + 1) / Gd;
