@@ -418,11 +418,13 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
     const bool two = row + 1 < X.r_hi;   // uniform over the group
     // lanes of the group's first warp that hold the two rows until they are finished
     const int ep0 = (2 * k) & 31, ep1 = ep0 + 1;
-    const float4 sc0 = srsc[0], sc1 = srsc[1];   // (the second is unused for a lone last row)
+    // a lone last row is processed twice (as both rows of the pair) and its second copy
+    // gets no weight: the hot loops carry no test for it
+    const float4 sc0 = srsc[0], sc1 = two ? srsc[1] : sc0;
     const float al0 = sc0.z, al1 = sc1.z;
     const f32x2 nk2 = pk(-X.kap, -X.kap);
     const float4* c0 = reinterpret_cast<const float4*>(srow);
-    const float4* c1 = reinterpret_cast<const float4*>(srow + X.ld);
+    const float4* c1 = reinterpret_cast<const float4*>(two ? srow + X.ld : srow);
     float4 e0[OT_BV], e1[OT_BV];
     float F0 = sc0.x, F1 = sc1.x, S0 = 0.f, S1 = 0.f;
     const bool first = X.t == 1;
@@ -438,10 +440,8 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
                 const float4 gg = CR.gc[g], cc = CR.cf[g];
                 e0[v] = exps4(c0[g], gg, nk2, F02);
                 S02 = dot4x2(e0[v], cc, S02);
-                if (two) {
-                    e1[v] = exps4(c1[g], gg, nk2, F12);
-                    S12 = dot4x2(e1[v], cc, S12);
-                }
+                e1[v] = exps4(c1[g], gg, nk2, F12);
+                S12 = dot4x2(e1[v], cc, S12);
             }
         }
         stage_release<STAGES>(P);
@@ -457,7 +457,7 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
     if (shifted) {
         // explicit shifts F_r = -max_j (gamma_j - kap c_rj), both rows
         const float4* r0 = first ? c0 : reinterpret_cast<const float4*>(X.Gp + (long long)row * X.ld);
-        const float4* r1 = first ? c1 : reinterpret_cast<const float4*>(X.Gp + (long long)(row + 1) * X.ld);
+        const float4* r1 = first ? c1 : reinterpret_cast<const float4*>(X.Gp + (long long)(two ? row + 1 : row) * X.ld);
         float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
         for (int v = 0; v < OT_BV; ++v) {
