@@ -134,18 +134,15 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 
-// Compensated (Kahan) addition on both lanes: sum + c carries the running total of
-// the added values to about one rounding, however many rows a thread accumulates.
-__device__ __forceinline__ void kahan2(f32x2& sum, f32x2& c, f32x2 v) {
-    const f32x2 y = sub2(v, c);
+// Compensated (Kahan) addition on both lanes of the contribution u0 e0 + u1 e1:
+// sum - nc carries the running total of the added values to about one rounding,
+// however many rows a thread accumulates (nc is the negated compensation, so the
+// contribution and the compensation enter through two FMAs).
+__device__ __forceinline__ void kahan2(f32x2& sum, f32x2& nc, f32x2 u0, f32x2 e0, f32x2 u1, f32x2 e1) {
+    const f32x2 y = fma2(u1, e1, fma2(u0, e0, nc));
     const f32x2 t = add2(sum, y);
-    c = sub2(sub2(t, sum), y);
+    nc = sub2(y, sub2(t, sum));
     sum = t;
 }
 
@@ -276,14 +273,16 @@ __device__ __forceinline__ void group_allreduce2(float& v0, float& v1, int gs, f
             s_part[(parity * OT_BW + (tid >> 5)) * 2 + 1] = v1;
         }
         group_barrier(gs, tid / gs);
-        const float id = MAX ? -INFINITY : 0.f;
-        float x0 = lane < nw ? s_part[(parity * OT_BW + w0 + lane) * 2] : id;
-        float x1 = lane < nw ? s_part[(parity * OT_BW + w0 + lane) * 2 + 1] : id;
+        // every aligned run of nw lanes holds the nw partials and combines them in the same tree
+        const float2 x = reinterpret_cast<const float2*>(s_part)[parity * OT_BW + w0 + (lane & (nw - 1))];
+        float x0 = x.x, x1 = x.y;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float a = __shfl_xor_sync(0xffffffffu, x0, o), b = __shfl_xor_sync(0xffffffffu, x1, o);
-            x0 = MAX ? fmaxf(x0, a) : x0 + a;
-            x1 = MAX ? fmaxf(x1, b) : x1 + b;
+            if (o < nw) {
+                const float a = __shfl_xor_sync(0xffffffffu, x0, o), b = __shfl_xor_sync(0xffffffffu, x1, o);
+                x0 = MAX ? fmaxf(x0, a) : x0 + a;
+                x1 = MAX ? fmaxf(x1, b) : x1 + b;
+            }
         }
         v0 = x0;
         v1 = x1;
@@ -521,8 +520,8 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
     const f32x2 u02 = pk(u0, u0), u12 = pk(u1, u1);
 #pragma unroll
     for (int v = 0; v < OT_BV; ++v) {
-        kahan2(acc[2 * v], cmp[2 * v], fma2(u12, pk(e1[v].x, e1[v].y), mul2(u02, pk(e0[v].x, e0[v].y))));
-        kahan2(acc[2 * v + 1], cmp[2 * v + 1], fma2(u12, pk(e1[v].z, e1[v].w), mul2(u02, pk(e0[v].z, e0[v].w))));
+        kahan2(acc[2 * v], cmp[2 * v], u02, pk(e0[v].x, e0[v].y), u12, pk(e1[v].x, e1[v].y));
+        kahan2(acc[2 * v + 1], cmp[2 * v + 1], u02, pk(e0[v].z, e0[v].w), u12, pk(e1[v].z, e1[v].w));
     }
 }
 
@@ -565,7 +564,7 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     CR.gc = reinterpret_cast<const float4*>(s_gc);
     CR.cf = reinterpret_cast<const float4*>(s_cf);
     int parity = 0;
-    f32x2 acc[2 * OT_BV], cmp[2 * OT_BV];   // column contributions (compensated sums)
+    f32x2 acc[2 * OT_BV], cmp[2 * OT_BV];   // column contributions: compensated sums acc - (-cmp)
 #pragma unroll
     for (int v = 0; v < 2 * OT_BV; ++v) acc[v] = cmp[v] = pk(0.f, 0.f);
     float l1 = 0.f;
@@ -598,8 +597,8 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
             const int g = gt + v * GS;
             if (g < X.ng4) {
                 const float4 cc = CR.cf[g];
-                const float2 s01 = upk(sub2(acc[2 * v], cmp[2 * v]));
-                const float2 s23 = upk(sub2(acc[2 * v + 1], cmp[2 * v + 1]));
+                const float2 s01 = upk(add2(acc[2 * v], cmp[2 * v]));
+                const float2 s23 = upk(add2(acc[2 * v + 1], cmp[2 * v + 1]));
                 const int j = 4 * g;
                 const long long o = d.v_off + j;
                 if (j < X.m) red_add_f32(A.R + o, s01.x * cc.x);
@@ -623,7 +622,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
     int* s_m = reinterpret_cast<int*>(dsm + BatchSmem::msz);                           // [count]
     int* s_act = reinterpret_cast<int*>(dsm + BatchSmem::act);                         // [count]
     int* s_rw = reinterpret_cast<int*>(dsm + BatchSmem::rw);                           // [count]
-    __shared__ float s_part[2 * OT_BW * 2];
+    __shared__ __align__(8) float s_part[2 * OT_BW * 2];
     __shared__ long long s_wsum[32];
     __shared__ double s_dred[OT_BW];
     __shared__ __align__(8) unsigned long long s_full[STAGES], s_empty[STAGES];
