@@ -38,6 +38,9 @@ __all__ = [
     "tile_marginal",
     "sector_problem",
     "image_grid_problem",
+    "mirror_order",
+    "mirror_images",
+    "mirror_problem",
     "polar_grid_problem",
     "paper_synthetic_problem",
     "batch_problems",
@@ -240,6 +243,77 @@ def image_grid_problem(side: int = 64, seed: int = 0, eps_frac: float = 0.01,
     meta = {"kind": "image_grid", "side": side, "seed": seed,
             "pixel_blocks": [np.stack(bk, 1) for bk in blocks]}
     return _finish(f"grid{side}_N4_s{seed}", m, N, a, b, eps_frac, C64, coords, coords.copy(), meta=meta)
+
+
+def mirror_order(h: int, w: int):
+    """Pixel order pi of the mirror vectorisation (Example 1, Eq. vectorization_mirror).
+
+    Returns (rows, cols), int64 [h*w].  Entries k < h*w/2 run over the left half
+    of the image column by column; entry k + h*w/2 is the pixel in the same row
+    and the mirrored column w-1-c.  An image that is symmetric about the
+    vertical axis therefore becomes a = (alpha; alpha), and any distance between
+    pixel positions becomes a 2-block circulant cost (the mirror is an isometry).
+    """
+    assert h > 0 and w > 0 and w % 2 == 0
+    k = np.arange(h * w, dtype=np.int64)
+    q = k // h
+    cols = np.where(k < h * w // 2, q, 3 * w // 2 - q - 1)
+    return k % h, cols
+
+
+def mirror_images(count: int, h: int = 64, w: int = 64, seed: int = 0, blobs: int = 4,
+                  asym: float = 0.0) -> np.ndarray:
+    """Gray-scale images symmetric about the vertical axis, float64 [count][h][w], each summing to 1.
+
+    Each image is a background of 2% of its peak plus ``blobs`` Gaussian blobs
+    with centres uniform in the left half (sigma ~ U[2, 8] px, amplitude ~
+    U[0.5, 1.5]); the right half is the exact mirror of the left.  ``asym`` > 0
+    then multiplies every pixel by (1 + asym * N(0, 1)) (clipped at 0), so the
+    symmetry is only approximate, as for photographs.
+    """
+    assert w % 2 == 0
+    rng = np.random.default_rng(seed)
+    rr, cc = np.meshgrid(np.arange(h) + 0.5, np.arange(w // 2) + 0.5, indexing="ij")
+    out = np.empty((count, h, w))
+    for i in range(count):
+        left = np.zeros((h, w // 2))
+        for _ in range(blobs):
+            cr, ccn = rng.uniform(0, h), rng.uniform(0, w / 2)
+            sig = rng.uniform(2.0, 8.0)
+            left += rng.uniform(0.5, 1.5) * np.exp(-((rr - cr) ** 2 + (cc - ccn) ** 2) / (2 * sig * sig))
+        left += 0.02 * left.max()
+        img = np.concatenate([left, left[:, ::-1]], axis=1)
+        if asym > 0.0:
+            img = np.maximum(img * (1.0 + asym * rng.standard_normal(img.shape)), 0.0)
+        out[i] = img / img.sum()
+    return out
+
+
+def mirror_problem(A: np.ndarray, B: np.ndarray, lam: float = 0.5) -> CyclicProblem:
+    """C-EROT between two h x w images under the mirror order (N = 2, m = h*w/2).
+
+    a and b are the images vectorised by ``mirror_order``; the cost is the
+    Euclidean distance between pixel positions, in pixels (the distance used
+    with the paper's real images), C_base[k][i][j] = |p_i - p_(k m + j)|.  The
+    base marginals are the block sums a_i + a_(m+i) (Alg. 3's block average up
+    to the factor 1/N; exact for symmetric images).  ``meta`` keeps the full
+    vectorised marginals (float64, unit mass) for the full and two-stage solves.
+    ``lam`` is the absolute regulariser (0.5 in the paper's experiments).
+    """
+    h, w = A.shape
+    rows, cols = mirror_order(h, w)
+    m = h * w // 2
+    a_full = _normalise(np.asarray(A, np.float64)[rows, cols])
+    b_full = _normalise(np.asarray(B, np.float64)[rows, cols])
+    r0, c0 = rows[:m], cols[:m]
+    C64 = np.empty((2, m, m))
+    for k in range(2):
+        dr = r0[:, None] - rows[k * m:(k + 1) * m][None, :]
+        dc = c0[:, None] - cols[k * m:(k + 1) * m][None, :]
+        C64[k] = np.sqrt((dr * dr + dc * dc).astype(np.float64))
+    meta = {"kind": "mirror", "h": h, "w": w, "a_full": a_full, "b_full": b_full}
+    return _finish(f"mirror{h}x{w}", m, 2, a_full[:m] + a_full[m:], b_full[:m] + b_full[m:], 0.0, C64,
+                   eps_abs=lam, meta=meta)
 
 
 def polar_grid_problem(n_radii: int = 256, n_angles: int = 16, N: int = 16, seed: int = 0,
