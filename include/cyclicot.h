@@ -404,6 +404,37 @@ int ot_kdomain_status(const void* workspace, int m, int* status, void* stream);
 int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* workspace, size_t ws_bytes,
                        void* stream);
 
+/* ---- C-SROT: a strongly convex regulariser other than the entropy -------- */
+
+/* Workspace bytes of ot_srot_reduced (0 if N m > 8192 or a size is <= 0). */
+size_t ot_srot_workspace_bytes(int m, int N);
+
+/*
+ * ot_srot_reduced -- Sec. 5.2 / Theorem 3 with the squared-L2 regulariser
+ * phi(x) = (lambda/2) x^2 on x >= 0: alternating minimisation of the reduced
+ * dual (Eq. dual_problem_cyclic_ROT), whose coordinate equations
+ * sum_{k,j} (phi*)'(w_i + z_j - C_ijk) = alpha_i (Eq.
+ * derivative_of_objective_function = 0, (phi*)'(y) = max(y, 0) / lambda) are
+ * solved exactly (Newton on the piecewise-linear left side); the optimal plan
+ * is T_ijk = max(w_i + z_j - C_ijk, 0) / lambda (Eq. optimality_condition).
+ *  C_base: [N][m][m] FP32 device (the first block row).  N = 1 is the plain
+ *     full problem.  N m <= 8192.
+ *  a_base, b_base: [m] FP32 device, positive; normalised internally so that
+ *     alpha, beta have mass 1/N.
+ *  opt: eps is lambda; tol_l1 (full-scale row L1 of the returned state),
+ *     max_iter, timeout_ns, warm_start (z holds the starting column potential).
+ *  w, z: [m] FP64 device outputs, the dual potentials of the mass-1/N reduced
+ *     problem.
+ *  out: iters, status, marg_l1 (row L1), value = N sum (C T + lambda T^2 / 2),
+ *     transport_cost = N sum C T (full scale); reserved[1] = 5.
+ *  workspace >= ot_srot_workspace_bytes(m, N), 256-byte aligned.  Asynchronous.
+ * Returns OT_ERR_ARG / OT_ERR_UNSUPPORTED / OT_ERR_WORKSPACE / OT_ERR_CUDA at
+ * launch; device-side outcomes are reported in out->status.
+ */
+int ot_srot_reduced(int m, int N, const float* a_base, const float* b_base, const float* C_base,
+                    const ot_options* opt, double* w, double* z, ot_result* out, void* workspace, size_t ws_bytes,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -168,7 +168,8 @@ def read_result(res: torch.Tensor) -> dict:
     r = ot_result.from_buffer_copy(raw)
     return {"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1, "marg_l2_col": r.marg_l2_col,
             "value": r.value, "transport_cost": r.transport_cost, "marg_l1_col": r.marg_l1_col,
-            "mass": r.reserved[0], "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream"}.get(r.reserved[1], "other")}
+            "mass": r.reserved[0],
+            "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream", 5.0: "srot"}.get(r.reserved[1], "other")}
 
 
 def ot_workspace_bytes(op: int, m_or_n: int, N: int, opt: Optional[ot_options] = None) -> int:
@@ -498,3 +499,43 @@ def two_stage(n: int, N: int, a, b, C, eps: float, stage1_l2: float = 1e-3, tol:
     o2 = options(eps, tol=tol, max_iter=max_iter, warm_start=True)
     f, g, r2 = ot_sinkhorn_full(n, a, b, C=C, opt=o2, g=g0, stream=stream)
     return f, g, read_result(r1), read_result(r2)
+
+
+# ------------------------------------------------------------------ C-SROT (squared-L2 regulariser)
+
+def _srot_lib():
+    L = lib()
+    if not getattr(L, "_srot_ready", False):
+        L.ot_srot_workspace_bytes.restype = ctypes.c_size_t
+        L.ot_srot_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.ot_srot_reduced.restype = ctypes.c_int
+        L.ot_srot_reduced.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(ot_options), _vp,
+                                      _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L._srot_ready = True
+    return L
+
+
+def srot_workspace(m: int, N: int, device) -> torch.Tensor:
+    nbytes = _srot_lib().ot_srot_workspace_bytes(int(m), int(N))
+    if nbytes == 0:
+        raise OTError(OT_ERR_UNSUPPORTED, "ot_srot_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def ot_srot_reduced(m: int, N: int, a_base, b_base, C_base, lam: float, tol: float = 1e-6, max_iter: int = 100000,
+                    w=None, z=None, out=None, ws=None, warm_start: bool = False, stream=None):
+    """C-SROT with phi(x) = (lam/2) x^2 (Sec. 5.2): alternating minimisation of the reduced dual.
+
+    Returns (w, z, out): FP64 dual potentials of the mass-1/N problem and the result record
+    (value and transport cost at full scale).  N = 1 solves the plain full problem.
+    """
+    dev = C_base.device
+    w = torch.empty(m, dtype=torch.float64, device=dev) if w is None else w
+    z = torch.zeros(m, dtype=torch.float64, device=dev) if z is None else z
+    out = new_result(dev) if out is None else out
+    ws = srot_workspace(m, N, dev) if ws is None else ws
+    opt = options(lam, tol=tol, max_iter=max_iter, warm_start=warm_start)
+    code = _srot_lib().ot_srot_reduced(int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(C_base), ctypes.byref(opt),
+                                       _ptr(w), _ptr(z), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "ot_srot_reduced")
+    return w, z, out
