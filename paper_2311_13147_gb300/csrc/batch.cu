@@ -147,10 +147,6 @@ __device__ __forceinline__ void kahan2(f32x2& sum, f32x2& nc, f32x2 u0, f32x2 e0
 }
 
 // ---- mbarrier helpers of the row engine
-__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive_cnt(unsigned long long* bar, unsigned cnt) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(cnt)
                  : "memory");

@@ -43,10 +43,6 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ int ld_volatile_int(const int* p) {
     return *((const volatile int*)p);
 }
@@ -170,91 +166,6 @@ __device__ __forceinline__ bool withhold_arrival(Ctrl* c, unsigned long long tim
     }
     __syncthreads();
     return false;
-}
-
-// ---- thread-block cluster helpers (distributed shared memory) ------------------
-
-__device__ __forceinline__ unsigned cluster_ctarank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ unsigned cluster_nctarank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-
-// Shared::cluster address of the same variable in CTA `rank` of this cluster.
-__device__ __forceinline__ unsigned mapa_rank(const void* p, unsigned rank) {
-    unsigned out;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_addr(p)), "r"(rank));
-    return out;
-}
-
-// Distributed-shared-memory loads.  Not volatile: the cluster barrier that
-// precedes every use orders them, and independent loads may then be batched.
-__device__ __forceinline__ float ld_dsmem_f32(unsigned caddr) {
-    float v;
-    asm("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(caddr));
-    return v;
-}
-
-__device__ __forceinline__ double ld_dsmem_f64(unsigned caddr) {
-    double v;
-    asm("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(caddr));
-    return v;
-}
-
-// Hardware cluster barrier: used once, right after the mbarriers are initialised
-// (no block can have left the kernel at that point).
-__device__ __forceinline__ void cluster_barrier_hw() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_remote_arrive(unsigned caddr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_cluster(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Cluster-wide barrier with a bounded wait: every block arrives on every
-// block's `cbar` (initialised with the cluster size), then waits on its own.
-// `phase` counts the cluster barriers this block has passed.  Returns false
-// (all threads) if the wait expired; OT_ERR_TIMEOUT is then recorded in `c`.
-__device__ __forceinline__ bool cluster_sync_bounded(unsigned long long* cbar, unsigned& phase, unsigned ncta,
-                                                     Ctrl* c, unsigned long long timeout_ns) {
-    __shared__ int s_cok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (unsigned r = 0; r < ncta; ++r) mbar_remote_arrive(mapa_rank(cbar, r));
-        int ok = 1;
-        if (!mbar_try_wait_cluster(cbar, phase & 1)) {
-            const unsigned long long t0 = globaltimer();
-            while (!mbar_try_wait_cluster(cbar, phase & 1)) {
-                if (globaltimer() - t0 > timeout_ns) {
-                    atomicCAS(&c->status, 0, OT_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        s_cok = ok;
-    }
-    phase += 1;
-    __syncthreads();
-    return s_cok != 0;
 }
 
 template <typename T>
