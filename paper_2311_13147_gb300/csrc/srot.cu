@@ -40,8 +40,8 @@ int device_sms();
 
 #define SR_BLOCK 256
 #define SR_WARPS (SR_BLOCK / 32)
-#define SR_VPT 32                             // terms per thread
-#define SR_MAX_ROW (SR_BLOCK * SR_VPT)        // N m <= 8192
+#define SR_VPT_MAX 32                         // terms per thread (16 for lines of <= 4096 terms)
+#define SR_MAX_ROW (SR_BLOCK * SR_VPT_MAX)    // N m <= 8192
 #define SR_NEWTON_MAX 64
 
 struct SrArgs {
@@ -96,12 +96,13 @@ __device__ __forceinline__ float block_max(float v, float* red) {
 // the number of active terms.  FP32 sums (a line has few active terms, and the
 // fixed reduction order gives every thread the same bits) and an exact integer
 // count; both in one block reduction.
-__device__ __forceinline__ void eval_side(const float (&u)[SR_VPT], int len, float delta, float2* red, float& h,
+template <int VPT>
+__device__ __forceinline__ void eval_side(const float (&u)[VPT], int len, float delta, float2* red, float& h,
                                           int& cnt) {
     float s = 0.f;
     int c = 0;
 #pragma unroll
-    for (int q = 0; q < SR_VPT; ++q) {
+    for (int q = 0; q < VPT; ++q) {
         const int idx = threadIdx.x + q * SR_BLOCK;
         const float x = delta + u[q];
         if (idx < len && x > 0.f) {
@@ -140,14 +141,15 @@ __device__ __forceinline__ void split_store(double v, float* hi, float* lo, int 
 // potential.  Returns the shift (FP64) and the left side at zero shift.  (Potentials
 // written by other blocks are read from L2: a line an SM cached in an earlier sweep
 // may be stale.)
+template <int VPT>
 __device__ double solve_line(const float* Cl, long long kstride, int m, int N, double p_self, const float* o_hi,
                              const float* o_lo, float target, float2* red, float* red_f, float& h0) {
     const int len = N * m;
     const float a_hi = (float)p_self, a_lo = (float)(p_self - (double)a_hi);
-    float u[SR_VPT];
+    float u[VPT];
     float umax = -INFINITY;
 #pragma unroll
-    for (int q = 0; q < SR_VPT; ++q) {
+    for (int q = 0; q < VPT; ++q) {
         const int idx = threadIdx.x + q * SR_BLOCK;
         u[q] = -INFINITY;
         if (idx < len) {
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(SR_BLOCK) srot_transpose_kernel(const float* _
     }
 }
 
+template <int VPT>
 __global__ void __launch_bounds__(SR_BLOCK) srot_kernel(SrArgs A) {
     __shared__ double s_red[SR_WARPS];
     __shared__ float2 s_red2[SR_WARPS];
@@ -257,8 +260,8 @@ __global__ void __launch_bounds__(SR_BLOCK) srot_kernel(SrArgs A) {
             float h0;
             const double al = (double)A.a[i] * ia;
             const double wi = __ldcg(A.w + cur * m + i);
-            const double d = solve_line(A.C + (long long)i * m, mm, m, N, wi, A.zh, A.zl, (float)(A.lam * al), s_red2,
-                                        s_redf, h0);
+            const double d = solve_line<VPT>(A.C + (long long)i * m, mm, m, N, wi, A.zh, A.zl, (float)(A.lam * al),
+                                             s_red2, s_redf, h0);
             if (tid == 0) {
                 A.w[nxt * m + i] = wi + d;
                 split_store(wi + d, A.wh + nxt * m, A.wl + nxt * m, i);
@@ -289,8 +292,8 @@ __global__ void __launch_bounds__(SR_BLOCK) srot_kernel(SrArgs A) {
         for (int j = B; j < m; j += G) {
             float h0;
             const double zj = __ldcg(A.z + j);
-            const double d = solve_line(A.Ct + (long long)j * m, mm, m, N, zj, A.wh + nxt * m, A.wl + nxt * m,
-                                        (float)(A.lam * (double)A.b[j] * ib), s_red2, s_redf, h0);
+            const double d = solve_line<VPT>(A.Ct + (long long)j * m, mm, m, N, zj, A.wh + nxt * m, A.wl + nxt * m,
+                                             (float)(A.lam * (double)A.b[j] * ib), s_red2, s_redf, h0);
             if (tid == 0) {
                 A.z[j] = zj + d;
                 split_store(zj + d, A.zh, A.zl, j);
@@ -413,8 +416,10 @@ extern "C" int ot_srot_reduced(int m, int N, const float* a_base, const float* b
     if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     const int sms = device_sms();
     if (sms <= 0) return OT_ERR_CUDA;
+    // a line's terms live in registers: 16 per thread while they fit, so that more blocks share an SM
+    auto kern = (long long)N * m <= SR_BLOCK * 16 ? srot_kernel<16> : srot_kernel<SR_VPT_MAX>;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, srot_kernel, SR_BLOCK, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SR_BLOCK, 0) != cudaSuccess || nb < 1)
         return OT_ERR_UNSUPPORTED;
     const int grid = sms * (nb < 4 ? nb : 4);
     cudaLaunchConfig_t cfg = {};
@@ -427,5 +432,5 @@ extern "C" int ot_srot_reduced(int m, int N, const float* a_base, const float* b
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, srot_kernel, A) == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+    return cudaLaunchKernelEx(&cfg, kern, A) == cudaSuccess ? OT_OK : OT_ERR_CUDA;
 }
