@@ -44,12 +44,9 @@ def coordinate_root(d: np.ndarray, target: float) -> float:
     the piece with p active terms w = (target + sum of the p smallest d) / p.
     """
     ds = np.sort(np.asarray(d, dtype=np.float64).ravel())
-    csum = np.cumsum(ds)
-    for p in range(1, ds.size + 1):
-        w = (target + csum[p - 1]) / p
-        if p == ds.size or w <= ds[p]:
-            return float(w)
-    raise AssertionError("unreachable")
+    w = (target + np.cumsum(ds)) / np.arange(1, ds.size + 1)     # candidate root on each piece
+    below_next = np.append(w[:-1] <= ds[1:], True)               # it lies on its piece
+    return float(w[int(np.argmax(below_next))])
 
 
 def srot_plan(w, z, C_base, lam) -> np.ndarray:

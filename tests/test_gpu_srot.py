@@ -94,3 +94,35 @@ def test_srot_argument_errors(cy):
     bad = dev(np.array([1, 1, 1, 0, 1, 1, 1, 1], np.float32))
     _, _, out = cy.ot_srot_reduced(8, 2, bad, x, C, 1.0)
     assert cy.read_result(out)["status"] == cy.OT_ERR_ARG
+
+
+def test_srot_wide_lines_certificate_and_full(cy):
+    """N m = 4400 > 4096 terms per line (the kernel keeps 32 terms per thread): the GPU's
+    potentials pass the optimality certificate (FP64 marginals and a vanishing primal-dual
+    gap), and the full problem (n = 4400, N = 1) gives the same objective in the same sweeps."""
+    p = I.sector_problem(1100, 4, seed=7)
+    lam = float(np.float32(1000.0))
+    tol = 1e-6
+    w, z, out = cy.ot_srot_reduced(p.m, p.N, dev(p.a_base), dev(p.b_base), dev(p.C_base), lam, tol=tol)
+    r = cy.read_result(out)
+    assert r["status"] == cy.OT_OK, r
+    C64 = p.C_base.astype(np.float64)
+    a64, b64 = np.asarray(p.a_base, np.float64), np.asarray(p.b_base, np.float64)
+    alpha, beta = a64 / a64.sum() / p.N, b64 / b64.sum() / p.N
+    wg, zg = w.cpu().numpy(), z.cpu().numpy()
+    T = SR.srot_plan(wg, zg, C64, lam)
+    rows = p.N * np.abs(T.sum(axis=(0, 2)) - alpha).sum()
+    cols = p.N * np.abs(T.sum(axis=(0, 1)) - beta).sum()
+    assert rows <= tol + 1e-7 and cols <= 1e-6, (rows, cols)
+    primal = SR.primal_value(T, C64, lam)["value"]
+    dual = SR.dual_value(wg, zg, alpha, beta, C64, lam)
+    assert primal == pytest.approx(dual, rel=1e-5)
+    assert r["value"] == pytest.approx(primal, rel=1e-9)
+    n = p.n
+    Cf = I.full_cost_from_blocks(p.C_base)
+    wf, zf, outf = cy.ot_srot_reduced(n, 1, dev(np.tile(p.a_base, p.N)), dev(np.tile(p.b_base, p.N)),
+                                      dev(Cf[None]), lam, tol=tol)
+    rf = cy.read_result(outf)
+    assert rf["status"] == cy.OT_OK, rf
+    assert r["value"] == pytest.approx(rf["value"], rel=1e-5)
+    assert abs(r["iters"] - rf["iters"]) <= 2, (r["iters"], rf["iters"])
