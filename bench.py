@@ -39,7 +39,7 @@ shifted to be non-negative, marginal blocks ~ U[0, 1); fold + reduced solve +
 compact unfold against the full GPU Sinkhorn on the stored d x d cost, both to
 1e-6; the paper's CPU timings (Table 1) are quoted beside them as context.
 
-``--workload mirror``: the paper's real-image setting (Sec. 6.2) on synthetic
+``--workload mirror``: the paper's real-image setting (Sec. 7.2) on synthetic
 stand-ins: 20 gray-scale images symmetric about the vertical axis up to 5%
 multiplicative noise, vectorised by the mirror order (N = 2), the cost the
 Euclidean distance between pixel positions, lambda = 0.5, all 190 pairs at
@@ -49,7 +49,7 @@ solve) and the two-stage Sinkhorn (Stage 1 to column L2 < 1e-3, Stage 2 to
 1e-6), each with its transport cost and ||T^T 1 - b||_2 against the images'
 own marginals (Table 2's columns); the paper's CPU times quoted as context.
 
-``--workload srot``: C-SROT with the squared-L2 regulariser (Sec. 5.2) on the
+``--workload srot``: C-SROT with the squared-L2 regulariser (Sec. 5.3) on the
 64 x 64 image grid (m = 1024, N = 4, n = 4096), lambda = 160 (about 8 active
 entries per row): the reduced alternating minimisation against the same
 method on the full problem (N = 1 on the assembled 4096 x 4096 cost), both to

@@ -410,7 +410,7 @@ int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* wo
 size_t ot_srot_workspace_bytes(int m, int N);
 
 /*
- * ot_srot_reduced -- Sec. 5.2 / Theorem 3 with the squared-L2 regulariser
+ * ot_srot_reduced -- Sec. 5.3 / Theorem 2 with the squared-L2 regulariser
  * phi(x) = (lambda/2) x^2 on x >= 0: alternating minimisation of the reduced
  * dual (Eq. dual_problem_cyclic_ROT), whose coordinate equations
  * sum_{k,j} (phi*)'(w_i + z_j - C_ijk) = alpha_i (Eq.

@@ -33,7 +33,7 @@ def marginal_errors(T: np.ndarray, a: np.ndarray, b: np.ndarray) -> dict:
     """Row / column marginal violations of Eq. problem_ROT's constraints.
 
     Returns the L1 row error sum_i |(T 1)_i - a_i|, the L1 column error and the
-    L2 column error ||T^T 1 - b||_2 that Sec. 6.1 reports.
+    L2 column error ||T^T 1 - b||_2 that Sec. 7.1 reports.
     """
     r = T.sum(axis=1) - a
     c = T.sum(axis=0) - b

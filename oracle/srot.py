@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
 bench.py's CPU baseline; never by the product path.
 
-Problem (Eq. problem_CROT with a strongly convex regulariser, Sec. 5.2):
+Problem (Eq. problem_CROT with a strongly convex regulariser, Sec. 5.3):
 
     min_{T_0..T_{N-1}}  sum_k <C_k, T_k> + sum_{k,i,j} phi(T_ijk)
     s.t.  sum_k T_k 1 = alpha,  sum_k T_k^T 1 = beta,
@@ -12,7 +12,7 @@ with phi(x) = (lam/2) x^2 for x >= 0 and +inf otherwise (the non-negativity of
 Eq. problem_ROT), alpha = a_base / N and beta = b_base / N (mass 1/N).
 
 phi*(y) = max(y, 0)^2 / (2 lam), (phi*)'(y) = max(y, 0) / lam.  The dual of
-Theorem 3 (Eq. dual_problem_cyclic_ROT) is maximised by alternating
+Theorem 2 (Eq. dual_problem_cyclic_ROT) is maximised by alternating
 minimisation over w and z: each coordinate w_i solves
 sum_{k,j} max(w_i + z_j - C_ijk, 0) / lam = alpha_i (Eq.
 derivative_of_objective_function set to zero), a monotone piecewise-linear
@@ -63,7 +63,7 @@ def row_error_l1(w, z, C_base, alpha, lam) -> float:
 
 
 def srot_reduced(a_base, b_base, C_base, lam, tol=1e-9, max_iter=100000, w0=None, z0=None):
-    """Alternating minimisation of the dual (Theorem 3) on the reduced problem.
+    """Alternating minimisation of the dual (Theorem 2) on the reduced problem.
 
     One iteration updates every w_i exactly for the current z, then every z_j
     for the new w.  Stops when the full-scale row L1 of the state after the z

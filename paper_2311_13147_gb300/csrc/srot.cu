@@ -1,4 +1,4 @@
-// C-SROT with the squared-L2 regulariser (Sec. 5.2, Theorem 3): alternating
+// C-SROT with the squared-L2 regulariser (Sec. 5.3, Theorem 2): alternating
 // minimisation of the reduced dual on the GPU.
 //
 // Problem (Eq. problem_CROT): min sum_k <C_k, T_k> + sum phi(T_ijk) subject to

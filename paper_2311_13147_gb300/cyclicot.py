@@ -524,7 +524,7 @@ def srot_workspace(m: int, N: int, device) -> torch.Tensor:
 
 def ot_srot_reduced(m: int, N: int, a_base, b_base, C_base, lam: float, tol: float = 1e-6, max_iter: int = 100000,
                     w=None, z=None, out=None, ws=None, warm_start: bool = False, stream=None):
-    """C-SROT with phi(x) = (lam/2) x^2 (Sec. 5.2): alternating minimisation of the reduced dual.
+    """C-SROT with phi(x) = (lam/2) x^2 (Sec. 5.3): alternating minimisation of the reduced dual.
 
     Returns (w, z, out): FP64 dual potentials of the mass-1/N problem and the result record
     (value and transport cost at full scale).  N = 1 solves the plain full problem.

@@ -355,7 +355,7 @@ def paper_synthetic_problem(m: int, N: int, seed: int = 0, lam: float = 0.5) -> 
     """Non-geometric blocks shaped like the paper's synthetic data (App. D).
 
     alpha, beta ~ U[0, 1) (then normalised); C_k entries ~ N(3, 5^2), shifted
-    by |min| over all blocks so that C >= 0; lambda = 0.5 (Sec. 6.1).
+    by |min| over all blocks so that C >= 0; lambda = 0.5 (Sec. 7.1).
     """
     rng = np.random.default_rng(seed)
     a = rng.uniform(0.0, 1.0, size=m)

@@ -1,10 +1,10 @@
-"""C-SROT (squared-L2 regulariser, Sec. 5.2) on the GPU against the FP64 oracle.
+"""C-SROT (squared-L2 regulariser, Sec. 5.3) on the GPU against the FP64 oracle.
 
 * image-grid and sector problems: objective and transport cost within 1e-5 of
   the oracle's, the plan's marginals in FP64 (row L1 <= tol + 1e-7, column
   L1 <= 1e-6; the solver's own L1, from FP32 row sums, within 1e-7 of the FP64
   one), potentials equal up to the dual's constant;
-* Theorem 3 on the GPU: the reduced solve and the plain full solve (N = 1 on
+* Theorem 2 on the GPU: the reduced solve and the plain full solve (N = 1 on
   the assembled n x n cost) give the same objective in the same number of
   sweeps (the alternating minimisation keeps symmetric iterates tiled);
 * argument errors.

@@ -1,4 +1,4 @@
-"""Pins of the C-SROT oracle (squared-L2 regulariser, Sec. 5.2 / Theorem 3).
+"""Pins of the C-SROT oracle (squared-L2 regulariser, Sec. 5.3 / Theorem 2).
 
 Each pin compares the oracle with something other than itself: an
 optimality certificate (feasibility plus a zero primal-dual gap), the full
@@ -44,7 +44,7 @@ def test_srot_optimality_certificate(m, N, seed, lam):
 
 @pytest.mark.parametrize("m,N,seed", [(5, 3, 3), (8, 4, 4)])
 def test_srot_reduced_equals_full(m, N, seed):
-    """Lemma 1 + Theorem 3: the full problem's unique optimum is the unfolded reduced one."""
+    """Lemma 1 + Theorem 2: the full problem's unique optimum is the unfolded reduced one."""
     lam = 0.2
     p = I.sector_problem(m, N, seed=seed)
     Cb = p.C_base.astype(np.float64)
