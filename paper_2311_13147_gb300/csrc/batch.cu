@@ -48,6 +48,8 @@ int device_sms();
 #define OT_BW (OT_BT / 32)
 #define OT_BV 4               // float4 column slots per thread and row
 #define OT_STAGES_MAX 2       // chunks in flight per block (bulk copies into shared memory)
+#define OT_ISSUER (OT_BT - 32) // issues the copies: lane 0 of the last warp (the first warp of a group
+                               // writes the pending potentials; a warp doing both lags at every reduction)
 #ifndef OT_ROW_FIXED
 #define OT_ROW_FIXED 8        // per-chunk cost of a group that does not scale with its slots, in slots
 #endif
@@ -324,7 +326,7 @@ __device__ __forceinline__ float hsum(f32x2 v) {
 // consumes them (across segments and sweeps); chunk n uses stage n % STAGES and
 // completes phase (n / STAGES) & 1 of that stage's full and empty barriers.
 // Every warp arrives once on a chunk's empty barrier when it no longer reads the
-// stage; thread 0 issues the copies.
+// stage; thread OT_ISSUER issues the copies.
 struct Pipe {
     float* stage;                 // [STAGES][2 * OT_BATCH_MAXM]
     float4* rsc;                  // [STAGES][2 * OT_BW] scalars of the chunk's rows
@@ -332,7 +334,7 @@ struct Pipe {
     unsigned long long* empty;    // [STAGES] (OT_BW arrivals)
     volatile int* abort;          // set by the first expired wait; later waits give up at once
     long long consumed;           // chunks consumed so far (every thread)
-    long long issued;             // chunks issued so far (thread 0)
+    long long issued;             // chunks issued so far (thread OT_ISSUER)
 };
 
 __device__ __forceinline__ void abort_block(const BatchArgs& A, const Pipe& P) {
@@ -349,7 +351,7 @@ __device__ __forceinline__ void stage_release(const Pipe& P) {
     if ((threadIdx.x & 31) == 0) mbar_arrive_cnt(&P.empty[P.consumed % STAGES], 1u);
 }
 
-// Chunk k of a segment (thread 0): rows r_lo + 2 k NG .. (2 NG consecutive rows,
+// Chunk k of a segment (thread OT_ISSUER): rows r_lo + 2 k NG .. (2 NG consecutive rows,
 // two per group) and their scalars, two bulk copies (rows are contiguous with
 // stride ld; all sizes and addresses 16-byte multiples).  The stage is taken
 // once every warp has released the chunk that used it before.  (No proxy fence
@@ -443,7 +445,7 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
         S0 = hsum(S02);
         S1 = hsum(S12);
         group_allreduce2<false>(S0, S1, GS, s_part, parity);
-        if (threadIdx.x == 0 && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
+        if (threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
         if (gt == ep0) l1 += fabsf(fmaf(S0, sc0.y - 1.0f, S0 - al0));
         if (two && gt == ep1) l1 += fabsf(fmaf(S1, sc1.y - 1.0f, S1 - al1));
         // uniform over the group
@@ -476,7 +478,7 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
         }
         if (first) stage_release<STAGES>(P);
         group_allreduce2<true>(m0, m1, GS, s_part, parity);
-        if (first && threadIdx.x == 0 && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
+        if (first && threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
         F0 = m0 > -INFINITY ? -m0 : 0.f;
         F1 = m1 > -INFINITY ? -m1 : 0.f;
         f32x2 S02 = pk(0.f, 0.f), S12 = pk(0.f, 0.f);
@@ -545,7 +547,7 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     X.t = t;
     X.kap = (float)(1.0 / ((double)d.eps * OT_LN2));
     X.nchunks = (r_hi - r_lo + 2 * NG - 1) / (2 * NG);
-    if (tid == 0) {
+    if (tid == OT_ISSUER) {
         for (int k = 0; k < X.nchunks && k < STAGES; ++k) issue_chunk<STAGES>(P, X, k, A);
     }
     // stage the column data (every thread has finished with the previous segment's)
@@ -722,7 +724,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         const long long TM = A.total_m;
         // ---------------- row phase
         // (the row scalars written last sweep by generic stores are read by bulk copies)
-        if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (tid == OT_ISSUER) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (int p = tid; p < count; p += OT_BT) s_act[p] = A.active[p];
         __syncthreads();
         batch_prefix(count, s_m, s_rw, s_act, true, s_pref, s_wsum);
@@ -839,7 +841,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
 fail:
     // no copy may still be writing into this block's shared memory when it exits (once the
     // block aborted no copy is issued, and at most the last STAGES issued can be in flight)
-    if (tid == 0) {
+    if (tid == OT_ISSUER) {
         for (long long u = P.issued > STAGES ? P.issued - STAGES : 0; u < P.issued; ++u)
             if (!mbar_wait(&s_full[u % STAGES], (unsigned)((u / STAGES) & 1), A.timeout_ns)) break;
         for (int p = B; p < count; p += Gd) {
