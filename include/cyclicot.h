@@ -435,6 +435,47 @@ int ot_srot_reduced(int m, int N, const float* a_base, const float* b_base, cons
                     const ot_options* opt, double* w, double* z, ot_result* out, void* workspace, size_t ws_bytes,
                     void* stream);
 
+/* ---- C-LOT: the small linear program of Theorem 1 ----------------------- */
+
+/* Workspace bytes of ot_lot_reduced for `count` problems of size m (0 if m > 5120 or a size is <= 0). */
+size_t ot_lot_workspace_bytes(int count, int m);
+
+/*
+ * ot_lot_reduced -- exact solve of the small LOT of Theorem 1 (Eq.
+ * small_problem_CLOT): min <G, S> subject to S 1 = alpha, S^T 1 = beta,
+ * S >= 0, by the network simplex that Sec. 5.2 names for it (primal network
+ * simplex on the complete bipartite graph; artificial-root start, block
+ * pricing, the strongly-feasible-tree leaving rule).  Its value times N is the
+ * value of the full C-LOT (Theorem 1 with mass 1/N blocks; the N block rows of
+ * the full plan are alike); ot_unfold_plan(OT_PLAN_LOT) turns S into the
+ * full plan (Eq. optimal_solution_problem_CLOT).  One thread block per
+ * problem; `count` problems of the same m in one launch.
+ *  G: [count][m][m] FP32 device, finite (ot_fold_cost(OT_MIN) output).
+ *  a_base, b_base: [count][m] FP32 device, >= 0 with positive sums; normalised
+ *     internally so that alpha, beta have mass 1/N.
+ *  opt: max_iter is the pivot cap per problem (>= 1); the other fields are
+ *     not used.
+ *  S: [count][m][m] FP32 device output, the optimal basic plan (at most 2m - 1
+ *     nonzeros per problem; the flows are kept in FP64 while pivoting).
+ *  u, v: [count][m] FP64 device outputs, optimal duals: u_i + v_j <= G_ij,
+ *     with equality where S_ij > 0; normalised to u_0 = 0.
+ *  out: [count] device results: iters = pivots, status, value = transport_cost
+ *     = N <G, S> (full scale, from the FP64 flows), reserved[0] = N (<alpha, u>
+ *     + <beta, v>) (equal to value at the optimum), marg_l1 / marg_l1_col /
+ *     marg_l2_col the full-scale marginal errors of the returned FP32 S,
+ *     reserved[1] = 6.  status OT_ERR_ARG for a negative or
+ *     non-finite entry or a zero sum (S, u, v are then NaN),
+ *     OT_ERR_NOT_CONVERGED when the pivot cap was reached (S then holds the
+ *     flows of the last basis on the original arcs; mass still on the
+ *     artificial start arcs leaves its marginals short, see marg_l1).
+ *  workspace >= ot_lot_workspace_bytes(count, m), 256-byte aligned.
+ *  Asynchronous.  Returns OT_ERR_ARG / OT_ERR_UNSUPPORTED (m > 5120) /
+ *  OT_ERR_WORKSPACE / OT_ERR_CUDA at launch.
+ */
+int ot_lot_reduced(int count, int m, int N, const float* a_base, const float* b_base, const float* G,
+                   const ot_options* opt, float* S, double* u, double* v, ot_result* out, void* workspace,
+                   size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,3 +177,28 @@ def brute_force_uniform(C) -> float:
     for perm in itertools.permutations(range(n)):
         best = min(best, C[rows, perm].sum())
     return float(best / n)
+
+
+def highs_lp(a, b, C) -> dict:
+    """min <C, S> s.t. S 1 = a, S^T 1 = b (b rescaled to the mass of a), S >= 0, by HiGHS.
+
+    A library LP solver used as an independent reference for larger problems
+    than ``transport_simplex`` handles; the equality constraints are assembled
+    sparse (2 M N nonzeros).
+    """
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix
+    C = np.asarray(C, np.float64)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    M, N = C.shape
+    idx = np.arange(M * N)
+    rows = np.concatenate([idx // N, M + idx % N])
+    A = coo_matrix((np.ones(2 * M * N), (rows, np.concatenate([idx, idx]))), shape=(M + N, M * N)).tocsr()
+    # solved at mass M (entries of order 1, well inside HiGHS's absolute feasibility tolerance), then rescaled
+    scale = M / a.sum()
+    res = linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([a * scale, b * (a.sum() * scale / b.sum())]),
+                  bounds=(0, None), method="highs")
+    if res.status != 0:
+        raise RuntimeError(f"HiGHS: {res.message}")
+    return {"value": float(res.fun) / scale, "S": res.x.reshape(M, N) / scale}

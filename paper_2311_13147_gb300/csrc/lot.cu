@@ -1,0 +1,473 @@
+// Reduced LOT of Theorem 1 on the GPU: the small linear program (Eq.
+// small_problem_CLOT)
+//
+//     min <G, S>  s.t.  S 1 = alpha,  S^T 1 = beta,  S >= 0,
+//
+// with G the min-fold of the cost blocks (Eq. definition_G) and alpha, beta the
+// base marginals (mass 1/N each).  Its optimal value is the C-LOT value, and
+// Eq. optimal_solution_problem_CLOT unfolds S into the block-circulant plan.
+// Sec. 5.2 solves this problem with the network simplex; so does this file, as
+// a primal network simplex on the complete bipartite graph of m sources
+// (nodes 0..m-1), m sinks (nodes m..2m-1) and an artificial root (node 2m):
+//
+//  start    every source sends its supply to the root and the root feeds every
+//           sink, over artificial arcs of cost M = (max|G| + 1)(2m + 1), a
+//           strongly feasible spanning tree (a zero-flow arc points away from
+//           the root);
+//  pricing  reduced costs G_ij - pi(i) + pi(m + j) of a block of rows, in
+//           parallel over the block's threads; the most negative one enters
+//           if it is below -tol, else the next block of rows is priced, and a
+//           full pass without a candidate proves optimality;
+//  pivot    one thread: the entering arc closes a cycle with the tree paths
+//           from its ends up to their common ancestor; the flow on the cycle's
+//           backward arcs bounds the step, and of the blocking arcs the last
+//           one met when going round the cycle from that ancestor leaves (the
+//           rule that keeps the tree strongly feasible, so degenerate pivots
+//           cannot cycle); the cut-off subtree is re-hung from the entering
+//           arc by reversing the parent pointers on the path between them;
+//  duals    every node's potential is the signed sum of arc costs on its path
+//           to the root (pi(x) = c + pi(parent) over an arc x -> parent,
+//           pi(x) = pi(parent) - c over parent -> x): recomputed from the tree
+//           after each pivot by pointer jumping (log2 depth rounds over all
+//           nodes in parallel), so no rounding drift accumulates.
+//
+// One thread block solves one problem and holds its tree in shared memory
+// (20 bytes per node); a launch solves `count` problems of one size at once.
+// Every loop has a bound; a tree found inconsistent ends the solve with
+// OT_ERR_NONFINITE instead of looping.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace cyc {
+
+#define LOT_BT 1024
+#define LOT_BW (LOT_BT / 32)
+#define LOT_MAXM 5120
+#define LOT_JC 4                                             // tree nodes per thread per jumping step
+#define LOT_PRICE_ARCS 16384                                 // arcs priced per step (whole rows)
+#define LOT_MAX_ROUNDS 20                                    // pointer-jumping rounds (2^20 > any depth)
+
+struct LotArgs {
+    int count, m, N;
+    const float* a;        // [count][m] unnormalised
+    const float* b;
+    const float* G;        // [count][m][m]
+    long long max_pivots;
+    float* S;              // [count][m][m]
+    double* u;             // [count][m]
+    double* v;
+    ot_result* res;        // [count]
+    double* flow;          // [count][2m + 1] flow on each node's parent arc (workspace)
+    double* sums;          // [count][2m] row and column sums of the returned plan (workspace)
+};
+
+// Block minimum of (value, index) pairs; ties go to the smaller index.  Every
+// thread returns the result.
+__device__ __forceinline__ void lot_argmin(double& v, int& idx, double* s_v, int* s_i) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov < v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    if (lane == 0) {
+        s_v[w] = v;
+        s_i[w] = idx;
+    }
+    __syncthreads();
+    if (w == 0) {
+        v = s_v[lane];
+        idx = s_i[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov < v || (ov == v && oi < idx)) {
+                v = ov;
+                idx = oi;
+            }
+        }
+        if (lane == 0) {
+            s_v[LOT_BW] = v;
+            s_i[LOT_BW] = idx;
+        }
+    }
+    __syncthreads();
+    v = s_v[LOT_BW];
+    idx = s_i[LOT_BW];
+}
+
+__device__ __forceinline__ double lot_sum(double x, double* s_v) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane == 0) s_v[w] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < LOT_BW; ++k) t += s_v[k];   // same order in every thread
+    return t;
+}
+
+// One pivot (a single thread).  Tree arrays: par (the root is its own parent),
+// ainf = 2 arc + up (arc = i m + j for an original arc, -1 for an artificial
+// one; up = 1 when the arc points from the node to its parent), flow on the
+// parent arc.  anc serves as the mark array here.  Returns 0 or an OT_ERR_*.
+__device__ int lot_pivot(int e, int m, int* par, int* ainf, int* anc, double* flow) {
+    const int V = 2 * m + 1, R = 2 * m;
+    const int u = e / m, v = m + (e - (e / m) * m);
+    // common ancestor w: mark the path from u to the root, climb from v to a mark
+    int x = u;
+    for (int s = 0;; ++s) {
+        if (s > V) return OT_ERR_NONFINITE;
+        anc[x] = -1;
+        if (x == R) break;
+        x = par[x];
+    }
+    int w = v;
+    for (int s = 0; anc[w] != -1; ++s) {
+        if (s > V) return OT_ERR_NONFINITE;
+        w = par[w];
+    }
+    // leaving arc: the cycle runs w -> ... -> u (down), u -> v, v -> ... -> w (up).
+    // Backward arcs: on the u side those pointing up, on the v side those pointing
+    // down.  Of the blocking arcs the last in that order leaves: on the u side the
+    // deepest (strict <, climbing from u), on the v side the highest (<=, climbing
+    // from v, and after every u-side arc).
+    double delta = INFINITY;
+    int leave = -1, leave_u = 0;
+    int len = 0;
+    for (x = u; x != w; x = par[x]) {
+        if (++len > V) return OT_ERR_NONFINITE;
+        if ((ainf[x] & 1) && flow[x] < delta) {
+            delta = flow[x];
+            leave = x;
+            leave_u = 1;
+        }
+    }
+    for (x = v; x != w; x = par[x]) {
+        if (++len > V) return OT_ERR_NONFINITE;
+        if (!(ainf[x] & 1) && flow[x] <= delta) {
+            delta = flow[x];
+            leave = x;
+            leave_u = 0;
+        }
+    }
+    if (leave < 0 || !(delta < INFINITY)) return OT_ERR_NONFINITE;   // cannot happen: every cycle has a backward arc
+    for (x = u; x != w; x = par[x]) flow[x] += (ainf[x] & 1) ? -delta : delta;
+    for (x = v; x != w; x = par[x]) flow[x] += (ainf[x] & 1) ? delta : -delta;
+    // re-hang: q is the entering arc's end inside the cut-off subtree; the path
+    // q -> ... -> leave is reversed, each node taking over its old child's arc
+    const int q = leave_u ? u : v;
+    int np = leave_u ? v : u;
+    int ninf = 2 * e + (leave_u ? 1 : 0);   // u -> v points up from u, down to v
+    double nfl = delta;
+    x = q;
+    for (int s = 0;; ++s) {
+        if (s > V) return OT_ERR_NONFINITE;
+        const int op = par[x], oinf = ainf[x];
+        const double ofl = flow[x];
+        par[x] = np;
+        ainf[x] = ninf;
+        flow[x] = nfl;
+        if (x == leave) break;
+        np = x;
+        ninf = oinf ^ 1;   // the same arc seen from the other end
+        nfl = ofl;
+        x = op;
+    }
+    return OT_OK;
+}
+
+__global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_constant__ LotArgs A) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int m = A.m, V = 2 * m + 1, R = 2 * m;
+    double* pi = reinterpret_cast<double*>(dsm);   // [V] node potentials
+    int* par = reinterpret_cast<int*>(pi + V);     // [V]
+    int* ainf = par + V;                           // [V]
+    int* anc = ainf + V;                           // [V] jump pointers (marks during a pivot)
+    __shared__ double s_v[LOT_BW + 1];
+    __shared__ int s_i[LOT_BW + 1];
+    __shared__ int s_err;
+
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const long long mm = (long long)m * m;
+    const float* G = A.G + (size_t)p * mm;
+    const float* a = A.a + (size_t)p * m;
+    const float* b = A.b + (size_t)p * m;
+    double* flow = A.flow + (size_t)p * V;
+    double* sums = A.sums + (size_t)p * 2 * m;
+    float* S = A.S + (size_t)p * mm;
+    ot_result* res = A.res + p;
+
+    // ---- marginal sums, cost bound and validation
+    double sa = 0.0, sb = 0.0;
+    int bad = 0;
+    for (int i = tid; i < m; i += LOT_BT) {
+        const float x = a[i], y = b[i];
+        bad |= !(x >= 0.f && x < INFINITY) || !(y >= 0.f && y < INFINITY);
+        sa += x;
+        sb += y;
+    }
+    float gmax = 0.f;
+    for (long long e = tid; e < mm; e += LOT_BT) {
+        const float c = fabsf(G[e]);
+        bad |= !(c < INFINITY);
+        gmax = fmaxf(gmax, c);
+    }
+    bad = __syncthreads_or(bad);
+    sa = lot_sum(sa, s_v);
+    sb = lot_sum(sb, s_v);
+    gmax = warp_max(gmax);
+    __syncthreads();
+    if ((tid & 31) == 0) s_v[tid >> 5] = gmax;
+    __syncthreads();
+    for (int k = 0; k < LOT_BW; ++k) gmax = fmaxf(gmax, (float)s_v[k]);
+    if (bad || !(sa > 0.0) || !(sb > 0.0)) {
+        for (long long e = tid; e < mm; e += LOT_BT) S[e] = NAN;
+        for (int i = tid; i < m; i += LOT_BT) {
+            A.u[(size_t)p * m + i] = NAN;
+            A.v[(size_t)p * m + i] = NAN;
+        }
+        if (tid == 0) {
+            res->iters = 0;
+            res->status = OT_ERR_ARG;
+            res->marg_l1 = res->marg_l1_col = res->marg_l2_col = -1.0;
+            res->value = res->transport_cost = NAN;
+            res->reserved[0] = NAN;
+            res->reserved[1] = 6.0;   // variant code: reduced LOT
+        }
+        return;
+    }
+    const double ia = 1.0 / (sa * (double)A.N), ib = 1.0 / (sb * (double)A.N);
+    const double M = ((double)gmax + 1.0) * (double)V;
+    const double tol = 1e-13 * M;   // reduced costs carry rounding of order 1e-15 M (potentials <= 2M)
+
+    // ---- strongly feasible artificial start
+    for (int x = tid; x < V; x += LOT_BT) {
+        par[x] = R;
+        anc[x] = R;   // no marks
+        if (x == R) {
+            ainf[x] = -2;
+            flow[x] = 0.0;
+            pi[x] = 0.0;
+        } else if (x < m) {
+            const double al = (double)a[x] * ia;
+            const int up = al > 0.0 ? 1 : 0;   // a zero supply hangs below the root with zero flow
+            ainf[x] = -2 + up;
+            flow[x] = al;
+            pi[x] = up ? M : -M;
+        } else {
+            ainf[x] = -2;                       // root -> sink
+            flow[x] = (double)b[x - m] * ib;
+            pi[x] = -M;
+        }
+    }
+    if (tid == 0) s_err = 0;
+
+    // ---- pivots
+    const int rb = max(1, min(m, LOT_PRICE_ARCS / m));   // rows per pricing step
+    const int npt = (V + LOT_BT - 1) / LOT_BT;            // tree nodes per thread
+    long long piv = 0;
+    int status = OT_OK;
+    int cursor = 0, scanned = 0;
+    for (;;) {
+        __syncthreads();   // potentials and the previous reduction's results are settled
+        const int r1 = min(m, cursor + rb);
+        double best = INFINITY;
+        int be = 0x7fffffff;
+        for (int r = cursor; r < r1; ++r) {
+            const double pr = pi[r];
+            const float* Gr = G + (size_t)r * m;
+            for (int j = tid; j < m; j += LOT_BT) {
+                const double rc = ((double)Gr[j] - pr) + pi[m + j];
+                if (rc < best) {
+                    best = rc;
+                    be = r * m + j;
+                }
+            }
+        }
+        lot_argmin(best, be, s_v, s_i);
+        scanned += r1 - cursor;
+        cursor = r1 == m ? 0 : r1;
+        if (!(best < -tol)) {
+            if (scanned >= m) break;   // a full pass found no improving arc: optimal
+            continue;
+        }
+        scanned = 0;
+        if (piv >= A.max_pivots) {
+            status = OT_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (tid == 0) s_err = lot_pivot(be, m, par, ainf, anc, flow);
+        __syncthreads();
+        if (s_err != OT_OK) {
+            status = s_err;
+            break;
+        }
+        ++piv;
+        // potentials by pointer jumping: pi[x] = pi(x) - pi(anc[x]) until anc[x] is the root
+        for (int k = 0; k < npt; ++k) {
+            const int x = tid + k * LOT_BT;
+            if (x < V) {
+                if (x == R) {
+                    anc[x] = R;
+                    pi[x] = 0.0;
+                } else {
+                    const int ai = ainf[x], arc = ai >> 1;
+                    const double c = arc >= 0 ? (double)G[arc] : M;
+                    anc[x] = par[x];
+                    pi[x] = (ai & 1) ? c : -c;
+                }
+            }
+        }
+        __syncthreads();
+        // a round reads (anc[y], pi[y]) of each owned node's y and then writes, LOT_JC owned
+        // nodes at a time: every pair is read either before or after its owner's write, so
+        // each read pair is consistent and pi[x] = pi(x) - pi(anc[x]) holds throughout
+        int rounds = 0;
+        for (;;) {
+            int any = 0;
+            for (int c0 = 0; c0 < npt; c0 += LOT_JC) {
+                int na[LOT_JC];
+                double dp[LOT_JC];
+#pragma unroll
+                for (int k = 0; k < LOT_JC; ++k) {
+                    const int x = tid + (c0 + k) * LOT_BT;
+                    na[k] = R;
+                    dp[k] = 0.0;
+                    if (x < V) {
+                        const int y = anc[x];
+                        if (y != R) {
+                            any = 1;
+                            na[k] = anc[y];
+                            dp[k] = pi[y];
+                        }
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < LOT_JC; ++k) {
+                    const int x = tid + (c0 + k) * LOT_BT;
+                    if (x < V && anc[x] != R) {
+                        pi[x] += dp[k];
+                        anc[x] = na[k];
+                    }
+                }
+                __syncthreads();
+            }
+            if (!__syncthreads_or(any)) break;
+            if (++rounds > LOT_MAX_ROUNDS) break;   // uniform; caught below
+        }
+        if (rounds > LOT_MAX_ROUNDS) {
+            status = OT_ERR_NONFINITE;
+            break;
+        }
+    }
+    __syncthreads();
+
+    // ---- outputs: the plan from the basic flows, duals u_i = pi(i) - pi(0), v_j = pi(0) - pi(m + j)
+    for (long long e = tid; e < mm; e += LOT_BT) S[e] = 0.f;
+    for (int k = tid; k < 2 * m; k += LOT_BT) sums[k] = 0.0;
+    __syncthreads();
+    double val = 0.0, art = 0.0;
+    for (int x = tid; x < V; x += LOT_BT) {
+        if (x == R) continue;
+        const int arc = ainf[x] >> 1;
+        if (arc >= 0) {
+            const float f = (float)flow[x];
+            S[arc] = f;
+            val += flow[x] * (double)G[arc];   // the LP value from the FP64 flows
+            const int i = arc / m, j = arc - i * m;
+            atomicAdd(&sums[i], (double)f);
+            atomicAdd(&sums[m + j], (double)f);
+        } else {
+            art += flow[x];
+        }
+    }
+    const double p0 = pi[0];
+    double dual = 0.0, l1r = 0.0, l1c = 0.0, l2c = 0.0;
+    __syncthreads();
+    for (int i = tid; i < m; i += LOT_BT) {
+        const double al = (double)a[i] * ia, be2 = (double)b[i] * ib;
+        const double ui = pi[i] - p0, vj = p0 - pi[m + i];
+        A.u[(size_t)p * m + i] = ui;
+        A.v[(size_t)p * m + i] = vj;
+        dual += al * ui + be2 * vj;
+        l1r += fabs(sums[i] - al);
+        const double dc = sums[m + i] - be2;
+        l1c += fabs(dc);
+        l2c += dc * dc;
+    }
+    val = lot_sum(val, s_v);
+    art = lot_sum(art, s_v);
+    dual = lot_sum(dual, s_v);
+    l1r = lot_sum(l1r, s_v);
+    l1c = lot_sum(l1c, s_v);
+    l2c = lot_sum(l2c, s_v);
+    if (tid == 0) {
+        // flow left on artificial arcs beyond rounding means M was too small (not expected)
+        if (status == OT_OK && art > 1e-9 / (double)A.N) status = OT_ERR_NOT_CONVERGED;
+        const double Nd = (double)A.N;
+        res->iters = (int)(piv < 0x7fffffff ? piv : 0x7fffffff);
+        res->status = status;
+        res->marg_l1 = Nd * l1r;            // full scale: the N row blocks of the plan are alike
+        res->marg_l1_col = Nd * l1c;
+        res->marg_l2_col = sqrt(Nd * l2c);
+        res->value = Nd * val;              // full scale: the C-LOT value is N <G, S> (mass 1/N, Theorem 1)
+        res->transport_cost = Nd * val;
+        res->reserved[0] = Nd * dual;       // N (<alpha, u> + <beta, v>): equals value at optimality
+        res->reserved[1] = 6.0;             // variant code: reduced LOT
+    }
+}
+
+size_t lot_smem_bytes(int m) { return (size_t)20 * (2 * (size_t)m + 1) + 16; }
+
+}  // namespace cyc
+
+using namespace cyc;
+
+static size_t lot_a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" size_t ot_lot_workspace_bytes(int count, int m) {
+    if (count <= 0 || m <= 0 || m > LOT_MAXM) return 0;
+    return lot_a256(sizeof(double) * (size_t)count * (2 * (size_t)m + 1)) +
+           lot_a256(sizeof(double) * (size_t)count * 2 * (size_t)m);
+}
+
+extern "C" int ot_lot_reduced(int count, int m, int N, const float* a_base, const float* b_base, const float* G,
+                              const ot_options* opt, float* S, double* u, double* v, ot_result* out, void* workspace,
+                              size_t ws_bytes, void* stream) {
+    if (count <= 0 || m <= 0 || N <= 0 || !a_base || !b_base || !G || !opt || !S || !u || !v || !out)
+        return OT_ERR_ARG;
+    if (opt->max_iter < 1) return OT_ERR_ARG;
+    if (m > LOT_MAXM) return OT_ERR_UNSUPPORTED;
+    const size_t need = ot_lot_workspace_bytes(count, m);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
+    LotArgs A;
+    memset(&A, 0, sizeof(A));
+    A.count = count;
+    A.m = m;
+    A.N = N;
+    A.a = a_base;
+    A.b = b_base;
+    A.G = G;
+    A.max_pivots = opt->max_iter;
+    A.S = S;
+    A.u = u;
+    A.v = v;
+    A.res = out;
+    A.flow = (double*)workspace;
+    A.sums = (double*)((char*)workspace + lot_a256(sizeof(double) * (size_t)count * (2 * (size_t)m + 1)));
+    const size_t smem = lot_smem_bytes(m);
+    if (cudaFuncSetAttribute(lot_simplex_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return OT_ERR_CUDA;
+    lot_simplex_kernel<<<count, LOT_BT, smem, (cudaStream_t)stream>>>(A);
+    return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}

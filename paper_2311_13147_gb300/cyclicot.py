@@ -169,7 +169,7 @@ def read_result(res: torch.Tensor) -> dict:
     return {"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1, "marg_l2_col": r.marg_l2_col,
             "value": r.value, "transport_cost": r.transport_cost, "marg_l1_col": r.marg_l1_col,
             "mass": r.reserved[0],
-            "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream", 5.0: "srot"}.get(r.reserved[1], "other")}
+            "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream", 5.0: "srot", 6.0: "lot"}.get(r.reserved[1], "other")}
 
 
 def ot_workspace_bytes(op: int, m_or_n: int, N: int, opt: Optional[ot_options] = None) -> int:
@@ -539,3 +539,56 @@ def ot_srot_reduced(m: int, N: int, a_base, b_base, C_base, lam: float, tol: flo
                                        _ptr(w), _ptr(z), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
     _check(code, "ot_srot_reduced")
     return w, z, out
+
+
+def _lot_lib():
+    L = lib()
+    if not getattr(L, "_lot_ready", False):
+        L.ot_lot_workspace_bytes.restype = ctypes.c_size_t
+        L.ot_lot_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.ot_lot_reduced.restype = ctypes.c_int
+        L.ot_lot_reduced.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                     ctypes.POINTER(ot_options), _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L._lot_ready = True
+    return L
+
+
+def lot_workspace(count: int, m: int, device) -> torch.Tensor:
+    nbytes = _lot_lib().ot_lot_workspace_bytes(int(count), int(m))
+    if nbytes == 0:
+        raise OTError(OT_ERR_UNSUPPORTED, "ot_lot_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def ot_lot_reduced(m: int, N: int, a_base, b_base, G, count: int = 1, max_pivots: Optional[int] = None,
+                   S=None, u=None, v=None, out=None, ws=None, stream=None):
+    """Small LOT of Theorem 1 by the network simplex: S [count][m][m] FP32, duals u, v [count][m] FP64.
+
+    a_base, b_base: [count][m] (or [m] when count = 1); G: [count][m][m] (or [m][m]), the min-fold.
+    Returns (S, u, v, out) with out a [count] result buffer (value = <G, S>, reserved[0] = dual value).
+    """
+    dev = G.device
+    S = torch.empty((count, m, m), dtype=torch.float32, device=dev) if S is None else S
+    u = torch.empty((count, m), dtype=torch.float64, device=dev) if u is None else u
+    v = torch.empty((count, m), dtype=torch.float64, device=dev) if v is None else v
+    if out is None:
+        out = torch.zeros((count, ctypes.sizeof(ot_result)), dtype=torch.uint8, device=dev)
+    ws = lot_workspace(count, m, dev) if ws is None else ws
+    opt = options(1.0, max_iter=int(max_pivots if max_pivots is not None else 100 * m + 10000))
+    code = _lot_lib().ot_lot_reduced(int(count), int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(G),
+                                     ctypes.byref(opt), _ptr(S), _ptr(u), _ptr(v), _ptr(out), _ptr(ws), ws.numel(),
+                                     _stream(stream))
+    _check(code, "ot_lot_reduced")
+    return S, u, v, out
+
+
+def read_lot_results(res: torch.Tensor, count: int):
+    """Host copies of the [count] records written by ot_lot_reduced."""
+    raw = bytes(res.cpu().numpy().tobytes())
+    out = []
+    for p in range(count):
+        r = ot_result.from_buffer_copy(raw[64 * p:64 * (p + 1)])
+        out.append({"pivots": r.iters, "status": r.status, "value": r.value, "dual": r.reserved[0],
+                    "marg_l1": r.marg_l1, "marg_l1_col": r.marg_l1_col, "marg_l2_col": r.marg_l2_col,
+                    "variant": "lot" if r.reserved[1] == 6.0 else "other"})
+    return out
