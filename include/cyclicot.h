@@ -458,7 +458,10 @@ size_t ot_lot_workspace_bytes(int count, int m);
  *  S: [count][m][m] FP32 device output, the optimal basic plan (at most 2m - 1
  *     nonzeros per problem; the flows are kept in FP64 while pivoting).
  *  u, v: [count][m] FP64 device outputs, optimal duals: u_i + v_j <= G_ij,
- *     with equality where S_ij > 0; normalised to u_0 = 0.
+ *     with equality where S_ij > 0, normalised to u_0 = 0.  The pivots run on
+ *     integer costs rint(G_ij 2^k), 2^k the largest power of two with
+ *     max |G| 2^k < 2^30, so these hold to 2^-k (about 1e-9 max |G|) and the
+ *     plan is optimal to 2^-k per unit of mass; reduced costs are exact.
  *  out: [count] device results: iters = pivots, status, value = transport_cost
  *     = N <G, S> (full scale, from the FP64 flows), reserved[0] = N (<alpha, u>
  *     + <beta, v>) (equal to value at the optimum), marg_l1 / marg_l1_col /

@@ -10,13 +10,19 @@
 // a primal network simplex on the complete bipartite graph of m sources
 // (nodes 0..m-1), m sinks (nodes m..2m-1) and an artificial root (node 2m):
 //
+//  costs    pivoting runs on integer costs: g_ij = rint(G_ij 2^k) with 2^k the
+//           largest power of two keeping |g| < 2^30, so reduced costs and
+//           potentials are exact 64-bit integers (no tolerance; FP64, slow on
+//           this GPU, stays out of the parallel loops).  The plan is optimal
+//           for these costs and within 2^-k per unit of mass, about
+//           1e-9 max|G|, of the optimum for the FP32 costs;
 //  start    every source sends its supply to the root and the root feeds every
-//           sink, over artificial arcs of cost M = (max|G| + 1)(2m + 1), a
+//           sink, over artificial arcs of cost M = (max|g| + 1)(2m + 1), a
 //           strongly feasible spanning tree (a zero-flow arc points away from
 //           the root);
-//  pricing  reduced costs G_ij - pi(i) + pi(m + j) of a block of rows, in
+//  pricing  reduced costs g_ij - pi(i) + pi(m + j) of a block of rows, in
 //           parallel over the block's threads; the most negative one enters
-//           if it is below -tol, else the next block of rows is priced, and a
+//           if it is negative, else the next block of rows is priced, and a
 //           full pass without a candidate proves optimality;
 //  pivot    one thread: the entering arc closes a cycle with the tree paths
 //           from its ends up to their common ancestor; the flow on the cycle's
@@ -31,8 +37,12 @@
 //           after each pivot by pointer jumping (log2 depth rounds over all
 //           nodes in parallel), so no rounding drift accumulates.
 //
-// One thread block solves one problem and holds its tree in shared memory
-// (20 bytes per node); a launch solves `count` problems of one size at once.
+// One thread block solves one problem and holds its tree in shared memory, 20
+// bytes per node: the int64 potential and the FP64 flow on the node's parent
+// arc, the parent and the arc's direction in 16 bits (an original arc is
+// fixed by its two ends, and points from the source to the sink; an arc to
+// the root is artificial), and a 16-bit jump pointer.  A launch solves
+// `count` problems of one size at once.
 // Every loop has a bound; a tree found inconsistent ends the solve with
 // OT_ERR_NONFINITE instead of looping.
 #include <math.h>
@@ -47,6 +57,7 @@ namespace cyc {
 #define LOT_MAXM 5120
 #define LOT_JC 4                                             // tree nodes per thread per jumping step
 #define LOT_PRICE_ARCS 16384                                 // arcs priced per step (whole rows)
+#define LOT_PPT (LOT_PRICE_ARCS / LOT_BT)                    // arcs per thread and step
 #define LOT_MAX_ROUNDS 20                                    // pointer-jumping rounds (2^20 > any depth)
 
 struct LotArgs {
@@ -59,17 +70,16 @@ struct LotArgs {
     double* u;             // [count][m]
     double* v;
     ot_result* res;        // [count]
-    double* flow;          // [count][2m + 1] flow on each node's parent arc (workspace)
     double* sums;          // [count][2m] row and column sums of the returned plan (workspace)
 };
 
 // Block minimum of (value, index) pairs; ties go to the smaller index.  Every
 // thread returns the result.
-__device__ __forceinline__ void lot_argmin(double& v, int& idx, double* s_v, int* s_i) {
+__device__ __forceinline__ void lot_argmin(long long& v, int& idx, long long* s_v, int* s_i) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (ov < v || (ov == v && oi < idx)) {
             v = ov;
@@ -86,7 +96,7 @@ __device__ __forceinline__ void lot_argmin(double& v, int& idx, double* s_v, int
         idx = s_i[lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
             const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
             if (ov < v || (ov == v && oi < idx)) {
                 v = ov;
@@ -114,25 +124,31 @@ __device__ __forceinline__ double lot_sum(double x, double* s_v) {
     return t;
 }
 
-// One pivot (a single thread).  Tree arrays: par (the root is its own parent),
-// ainf = 2 arc + up (arc = i m + j for an original arc, -1 for an artificial
-// one; up = 1 when the arc points from the node to its parent), flow on the
-// parent arc.  anc serves as the mark array here.  Returns 0 or an OT_ERR_*.
-__device__ int lot_pivot(int e, int m, int* par, int* ainf, int* anc, double* flow) {
+#define LOT_MARK 0xffffu
+
+// Original arc between node x and its parent y (one a source, the other a sink).
+__device__ __forceinline__ int lot_arc(int x, int y, int m) {
+    return x < m ? x * m + (y - m) : y * m + (x - m);
+}
+
+// One pivot (a single thread).  pu[x] = 2 parent + up (up = 1 when x's parent
+// arc points from x to the parent; the root is its own parent), flow[x] the
+// flow on that arc; anc serves as the mark array here.  Returns 0 or an OT_ERR_*.
+__device__ int lot_pivot(int e, int m, unsigned short* pu, unsigned short* anc, double* flow) {
     const int V = 2 * m + 1, R = 2 * m;
     const int u = e / m, v = m + (e - (e / m) * m);
     // common ancestor w: mark the path from u to the root, climb from v to a mark
     int x = u;
     for (int s = 0;; ++s) {
         if (s > V) return OT_ERR_NONFINITE;
-        anc[x] = -1;
+        anc[x] = LOT_MARK;
         if (x == R) break;
-        x = par[x];
+        x = pu[x] >> 1;
     }
     int w = v;
-    for (int s = 0; anc[w] != -1; ++s) {
+    for (int s = 0; anc[w] != LOT_MARK; ++s) {
         if (s > V) return OT_ERR_NONFINITE;
-        w = par[w];
+        w = pu[w] >> 1;
     }
     // leaving arc: the cycle runs w -> ... -> u (down), u -> v, v -> ... -> w (up).
     // Backward arcs: on the u side those pointing up, on the v side those pointing
@@ -142,42 +158,43 @@ __device__ int lot_pivot(int e, int m, int* par, int* ainf, int* anc, double* fl
     double delta = INFINITY;
     int leave = -1, leave_u = 0;
     int len = 0;
-    for (x = u; x != w; x = par[x]) {
+    for (x = u; x != w; x = pu[x] >> 1) {
         if (++len > V) return OT_ERR_NONFINITE;
-        if ((ainf[x] & 1) && flow[x] < delta) {
+        if ((pu[x] & 1) && flow[x] < delta) {
             delta = flow[x];
             leave = x;
             leave_u = 1;
         }
     }
-    for (x = v; x != w; x = par[x]) {
+    for (x = v; x != w; x = pu[x] >> 1) {
         if (++len > V) return OT_ERR_NONFINITE;
-        if (!(ainf[x] & 1) && flow[x] <= delta) {
+        if (!(pu[x] & 1) && flow[x] <= delta) {
             delta = flow[x];
             leave = x;
             leave_u = 0;
         }
     }
     if (leave < 0 || !(delta < INFINITY)) return OT_ERR_NONFINITE;   // cannot happen: every cycle has a backward arc
-    for (x = u; x != w; x = par[x]) flow[x] += (ainf[x] & 1) ? -delta : delta;
-    for (x = v; x != w; x = par[x]) flow[x] += (ainf[x] & 1) ? delta : -delta;
+    for (x = u; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? -delta : delta;
+    for (x = v; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? delta : -delta;
     // re-hang: q is the entering arc's end inside the cut-off subtree; the path
     // q -> ... -> leave is reversed, each node taking over its old child's arc
+    // (the reversed path holds original arcs only: an artificial arc joins a node
+    // to the root, which stays above the leaving arc)
     const int q = leave_u ? u : v;
     int np = leave_u ? v : u;
-    int ninf = 2 * e + (leave_u ? 1 : 0);   // u -> v points up from u, down to v
+    int nup = leave_u ? 1 : 0;   // u -> v points up from u, down to v
     double nfl = delta;
     x = q;
     for (int s = 0;; ++s) {
         if (s > V) return OT_ERR_NONFINITE;
-        const int op = par[x], oinf = ainf[x];
+        const int op = pu[x] >> 1, oup = pu[x] & 1;
         const double ofl = flow[x];
-        par[x] = np;
-        ainf[x] = ninf;
+        pu[x] = (unsigned short)(2 * np + nup);
         flow[x] = nfl;
         if (x == leave) break;
         np = x;
-        ninf = oinf ^ 1;   // the same arc seen from the other end
+        nup = oup ^ 1;   // the same arc seen from the other end
         nfl = ofl;
         x = op;
     }
@@ -187,11 +204,12 @@ __device__ int lot_pivot(int e, int m, int* par, int* ainf, int* anc, double* fl
 __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_constant__ LotArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
     const int m = A.m, V = 2 * m + 1, R = 2 * m;
-    double* pi = reinterpret_cast<double*>(dsm);   // [V] node potentials
-    int* par = reinterpret_cast<int*>(pi + V);     // [V]
-    int* ainf = par + V;                           // [V]
-    int* anc = ainf + V;                           // [V] jump pointers (marks during a pivot)
+    long long* pi = reinterpret_cast<long long*>(dsm);                    // [V] node potentials (integer costs)
+    double* flow = reinterpret_cast<double*>(pi + V);                     // [V] flow on the parent arc
+    unsigned short* pu = reinterpret_cast<unsigned short*>(flow + V);     // [V] 2 parent + up
+    unsigned short* anc = pu + V;                                         // [V] jump pointers (marks in a pivot)
     __shared__ double s_v[LOT_BW + 1];
+    __shared__ long long s_q[LOT_BW + 1];
     __shared__ int s_i[LOT_BW + 1];
     __shared__ int s_err;
 
@@ -200,7 +218,6 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     const float* G = A.G + (size_t)p * mm;
     const float* a = A.a + (size_t)p * m;
     const float* b = A.b + (size_t)p * m;
-    double* flow = A.flow + (size_t)p * V;
     double* sums = A.sums + (size_t)p * 2 * m;
     float* S = A.S + (size_t)p * mm;
     ot_result* res = A.res + p;
@@ -245,25 +262,26 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         return;
     }
     const double ia = 1.0 / (sa * (double)A.N), ib = 1.0 / (sb * (double)A.N);
-    const double M = ((double)gmax + 1.0) * (double)V;
-    const double tol = 1e-13 * M;   // reduced costs carry rounding of order 1e-15 M (potentials <= 2M)
+    // integer costs rint(G 2^k) with |g| < 2^30; |potentials| <= 2 M + V 2^30 < 2^46
+    const int k2 = gmax > 0.f ? min(100, max(-120, 29 - ilogbf(gmax))) : 0;
+    const float sc = ldexpf(1.0f, k2);
+    const long long M = ((long long)ldexpf(gmax, k2) + 1) * (long long)V;
 
     // ---- strongly feasible artificial start
     for (int x = tid; x < V; x += LOT_BT) {
-        par[x] = R;
-        anc[x] = R;   // no marks
+        anc[x] = (unsigned short)R;   // no marks
         if (x == R) {
-            ainf[x] = -2;
+            pu[x] = (unsigned short)(2 * R);
             flow[x] = 0.0;
             pi[x] = 0.0;
         } else if (x < m) {
             const double al = (double)a[x] * ia;
             const int up = al > 0.0 ? 1 : 0;   // a zero supply hangs below the root with zero flow
-            ainf[x] = -2 + up;
+            pu[x] = (unsigned short)(2 * R + up);
             flow[x] = al;
             pi[x] = up ? M : -M;
         } else {
-            ainf[x] = -2;                       // root -> sink
+            pu[x] = (unsigned short)(2 * R);   // root -> sink
             flow[x] = (double)b[x - m] * ib;
             pi[x] = -M;
         }
@@ -271,7 +289,8 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     if (tid == 0) s_err = 0;
 
     // ---- pivots
-    const int rb = max(1, min(m, LOT_PRICE_ARCS / m));   // rows per pricing step
+    const int rb = max(1, min(m, LOT_PRICE_ARCS / m));   // rows per pricing step (rb m <= LOT_PRICE_ARCS)
+    const int qstep = LOT_BT / m, rstep = LOT_BT - (LOT_BT / m) * m;
     const int npt = (V + LOT_BT - 1) / LOT_BT;            // tree nodes per thread
     long long piv = 0;
     int status = OT_OK;
@@ -279,23 +298,35 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     for (;;) {
         __syncthreads();   // potentials and the previous reduction's results are settled
         const int r1 = min(m, cursor + rb);
-        double best = INFINITY;
+        long long best = 0x7fffffffffffffffll;
         int be = 0x7fffffff;
-        for (int r = cursor; r < r1; ++r) {
-            const double pr = pi[r];
-            const float* Gr = G + (size_t)r * m;
-            for (int j = tid; j < m; j += LOT_BT) {
-                const double rc = ((double)Gr[j] - pr) + pi[m + j];
-                if (rc < best) {
-                    best = rc;
-                    be = r * m + j;
+        {
+            // arcs e = cursor m + tid + k LOT_BT of rows [cursor, r1): all loads issued up front
+            const int e_end = r1 * m;
+            int e = cursor * m + tid;
+            int r = e / m, j = e - r * m;
+#pragma unroll
+            for (int k = 0; k < LOT_PPT; ++k) {
+                if (e < e_end) {
+                    const long long rc = (long long)__float2int_rn(G[e] * sc) - pi[r] + pi[m + j];
+                    if (rc < best) {
+                        best = rc;
+                        be = e;
+                    }
+                }
+                e += LOT_BT;
+                j += rstep;
+                r += qstep;
+                if (j >= m) {
+                    j -= m;
+                    ++r;
                 }
             }
         }
-        lot_argmin(best, be, s_v, s_i);
+        lot_argmin(best, be, s_q, s_i);
         scanned += r1 - cursor;
         cursor = r1 == m ? 0 : r1;
-        if (!(best < -tol)) {
+        if (best >= 0) {
             if (scanned >= m) break;   // a full pass found no improving arc: optimal
             continue;
         }
@@ -304,7 +335,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             status = OT_ERR_NOT_CONVERGED;
             break;
         }
-        if (tid == 0) s_err = lot_pivot(be, m, par, ainf, anc, flow);
+        if (tid == 0) s_err = lot_pivot(be, m, pu, anc, flow);
         __syncthreads();
         if (s_err != OT_OK) {
             status = s_err;
@@ -316,13 +347,13 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             const int x = tid + k * LOT_BT;
             if (x < V) {
                 if (x == R) {
-                    anc[x] = R;
+                    anc[x] = (unsigned short)R;
                     pi[x] = 0.0;
                 } else {
-                    const int ai = ainf[x], arc = ai >> 1;
-                    const double c = arc >= 0 ? (double)G[arc] : M;
-                    anc[x] = par[x];
-                    pi[x] = (ai & 1) ? c : -c;
+                    const int y = pu[x] >> 1;
+                    const long long c = y == R ? M : (long long)__float2int_rn(G[lot_arc(x, y, m)] * sc);
+                    anc[x] = (unsigned short)y;
+                    pi[x] = (pu[x] & 1) ? c : -c;
                 }
             }
         }
@@ -335,12 +366,12 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             int any = 0;
             for (int c0 = 0; c0 < npt; c0 += LOT_JC) {
                 int na[LOT_JC];
-                double dp[LOT_JC];
+                long long dp[LOT_JC];
 #pragma unroll
                 for (int k = 0; k < LOT_JC; ++k) {
                     const int x = tid + (c0 + k) * LOT_BT;
                     na[k] = R;
-                    dp[k] = 0.0;
+                    dp[k] = 0;
                     if (x < V) {
                         const int y = anc[x];
                         if (y != R) {
@@ -378,8 +409,9 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     double val = 0.0, art = 0.0;
     for (int x = tid; x < V; x += LOT_BT) {
         if (x == R) continue;
-        const int arc = ainf[x] >> 1;
-        if (arc >= 0) {
+        const int y = pu[x] >> 1;
+        if (y != R) {
+            const int arc = lot_arc(x, y, m);
             const float f = (float)flow[x];
             S[arc] = f;
             val += flow[x] * (double)G[arc];   // the LP value from the FP64 flows
@@ -390,12 +422,13 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             art += flow[x];
         }
     }
-    const double p0 = pi[0];
+    const long long p0 = pi[0];
+    const double unit = ldexp(1.0, -k2);
     double dual = 0.0, l1r = 0.0, l1c = 0.0, l2c = 0.0;
     __syncthreads();
     for (int i = tid; i < m; i += LOT_BT) {
         const double al = (double)a[i] * ia, be2 = (double)b[i] * ib;
-        const double ui = pi[i] - p0, vj = p0 - pi[m + i];
+        const double ui = (double)(pi[i] - p0) * unit, vj = (double)(p0 - pi[m + i]) * unit;
         A.u[(size_t)p * m + i] = ui;
         A.v[(size_t)p * m + i] = vj;
         dual += al * ui + be2 * vj;
@@ -427,6 +460,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
 }
 
 size_t lot_smem_bytes(int m) { return (size_t)20 * (2 * (size_t)m + 1) + 16; }
+static_assert(2 * (2 * LOT_MAXM + 1) < 0xffff, "parent and direction fit 16 bits, below the mark");
 
 }  // namespace cyc
 
@@ -436,8 +470,7 @@ static size_t lot_a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 extern "C" size_t ot_lot_workspace_bytes(int count, int m) {
     if (count <= 0 || m <= 0 || m > LOT_MAXM) return 0;
-    return lot_a256(sizeof(double) * (size_t)count * (2 * (size_t)m + 1)) +
-           lot_a256(sizeof(double) * (size_t)count * 2 * (size_t)m);
+    return lot_a256(sizeof(double) * (size_t)count * 2 * (size_t)m);
 }
 
 extern "C" int ot_lot_reduced(int count, int m, int N, const float* a_base, const float* b_base, const float* G,
@@ -462,8 +495,7 @@ extern "C" int ot_lot_reduced(int count, int m, int N, const float* a_base, cons
     A.u = u;
     A.v = v;
     A.res = out;
-    A.flow = (double*)workspace;
-    A.sums = (double*)((char*)workspace + lot_a256(sizeof(double) * (size_t)count * (2 * (size_t)m + 1)));
+    A.sums = (double*)workspace;
     const size_t smem = lot_smem_bytes(m);
     if (cudaFuncSetAttribute(lot_simplex_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
