@@ -975,13 +975,7 @@ def run_ours_lot(args, rank, world, local_rank):
 
     def row(d, N, steps, warmup, seed):
         m = d // N
-        g = torch.Generator(device=dev)
-        g.manual_seed(seed)
-        # the paper's recipe (App. D): cost blocks ~ N(3, 5^2) shifted by |min| per instance, marginals ~ U[0, 1)
-        Cb = torch.randn((K, N, m, m), generator=g, device=dev, dtype=torch.float32).mul_(5.0).add_(3.0)
-        Cb.add_(Cb.view(K, -1).amin(dim=1).abs().view(K, 1, 1, 1))
-        a = torch.rand((K, m), generator=g, device=dev, dtype=torch.float32)
-        b = torch.rand((K, m), generator=g, device=dev, dtype=torch.float32)
+        Cb, a, b = I.paper_synthetic_device(K, m, N, seed, dev)   # the paper's recipe (App. D), on the device
         G = torch.empty((K, m, m), dtype=torch.float32, device=dev)
         ks = torch.empty((K, m, m), dtype=torch.uint8, device=dev)
         T = torch.empty((K, N, m, m), dtype=torch.float32, device=dev)

@@ -366,6 +366,25 @@ def paper_synthetic_problem(m: int, N: int, seed: int = 0, lam: float = 0.5) -> 
                    meta={"kind": "paper_synthetic", "seed": seed})
 
 
+def paper_synthetic_device(count: int, m: int, N: int, seed: int, device):
+    """`count` instances of the paper's synthetic setting (App. D) drawn on the device.
+
+    Cost blocks C_k ~ N(3, 5^2) shifted by |min| over each instance's blocks,
+    marginal blocks ~ U[0, 1) (normalised by the solvers), from torch's seeded
+    device generator: shapes and distributions of ``paper_synthetic_problem``
+    for sizes whose host generation would take minutes (d = 10000 rows).
+    Returns (C_base [count][N][m][m], a_base [count][m], b_base [count][m]), FP32.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    C = torch.randn((count, N, m, m), generator=g, device=device, dtype=torch.float32).mul_(5.0).add_(3.0)
+    C.add_(C.view(count, -1).amin(dim=1).abs().view(count, 1, 1, 1))
+    a = torch.rand((count, m), generator=g, device=device, dtype=torch.float32)
+    b = torch.rand((count, m), generator=g, device=device, dtype=torch.float32)
+    return C, a, b
+
+
 def batch_problems(count: int = 512, seed: int = 0, n_lo: int = 1024, n_hi: int = 16384,
                    orders=(2, 3, 4, 6, 8), eps_frac: float = 0.01, dirichlet: float = 0.5,
                    with_cost: bool = False):
