@@ -265,6 +265,30 @@ def test_clot_reduction_brute_force(m, N):
     assert e["row_l1"] < 1e-14 and e["col_l1"] < 1e-14
 
 
+@pytest.mark.parametrize("n", [4, 6])
+def test_highs_lp_pinned(n):
+    """The oracle's sparse HiGHS wrapper (the reference of the GPU LOT tests) against brute force over
+    permutations (uniform marginals), an assignment solver, and the oracle's own simplex on general masses."""
+    pytest.importorskip("scipy")
+    from scipy.optimize import linear_sum_assignment
+    rng = np.random.default_rng(100 + n)
+    C = rng.uniform(0, 1, size=(n, n))
+    u = np.full(n, 1.0 / n)
+    h = OL.highs_lp(u, u, C)
+    assert h["value"] == pytest.approx(OL.brute_force_uniform(C), abs=1e-12)
+    ri, ci = linear_sum_assignment(C)
+    assert h["value"] == pytest.approx(C[ri, ci].sum() / n, abs=1e-12)
+    # general masses with a zero supply
+    a = rng.uniform(0, 1, size=n)
+    b = rng.uniform(0, 1, size=n)
+    a[0] = 0.0
+    a, b = a / a.sum() / 3.0, b / b.sum() / 3.0
+    r = OL.transport_simplex(a, b, C)
+    h = OL.highs_lp(a, b, C)
+    assert h["value"] == pytest.approx(r["value"], rel=1e-9)
+    assert np.abs(h["S"].sum(1) - a).max() < 1e-9 and np.abs(h["S"].sum(0) - b).max() < 1e-9
+
+
 def _highs(a, b, C):
     from scipy.optimize import linprog
     M, N = C.shape
