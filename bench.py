@@ -412,6 +412,36 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_lot(args, rank, world):
+    """The oracle on the C-LOT workload: per step one instance of the headline row (d = 10000, N = 10),
+    FP64 min-fold and the small LOT by HiGHS (oracle.lot.highs_lp)."""
+    from oracle import lot as OL
+    from oracle import sinkhorn as OS
+    from paper_2311_13147_gb300 import inputs as I
+    times, cores = [], []
+    for s in range(args.warmup + args.steps):
+        p = I.paper_synthetic_problem(1000, 10, seed=s)
+        t0, c0 = time.perf_counter(), time.process_time()
+        G, _ = OS.fold_min(p.C_base.astype(np.float64))
+        al, be = OS.base_marginals(p.a_base, p.b_base, p.N)
+        OL.highs_lp(al, be, G)
+        wall = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(wall)
+            cores.append((time.process_time() - c0) / wall)
+    t = float(np.mean(times))
+    value = 1.0 / t
+    return {"metric": "C-LOT solves/s (fold + small LOT by network simplex + unfold)", "value": value,
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded; the paper's recipe)",
+            "config": {"workload": "paper_table1_lot_d10000_N10_m1000 (one instance per step)"}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": max(1, round(float(np.mean(cores)))),
+                             "kind": "oracle", "sample": "one instance per step: numpy FP64 min-fold + HiGHS on "
+                                                         "the small LOT (no unfold)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 # ---------------------------------------------------------------- batch workload
 
 def batch_workload(args, rank=0):
@@ -1291,6 +1321,8 @@ def main():
             return
         if args.workload == "batch":
             print(json.dumps(run_reference_batch(args, rank, world)))
+        elif args.workload == "lot":
+            print(json.dumps(run_reference_lot(args, rank, world)))
         else:
             print(json.dumps(run_reference(args, rank, world)))
         return
