@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         if (x == R) {
             pu[x] = (unsigned short)(2 * R);
             flow[x] = 0.0;
-            pi[x] = 0.0;
+            pi[x] = 0;
         } else if (x < m) {
             const double al = (double)a[x] * ia;
             const int up = al > 0.0 ? 1 : 0;   // a zero supply hangs below the root with zero flow
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             if (x < V) {
                 if (x == R) {
                     anc[x] = (unsigned short)R;
-                    pi[x] = 0.0;
+                    pi[x] = 0;
                 } else {
                     const int y = pu[x] >> 1;
                     const long long c = y == R ? M : (long long)__float2int_rn(G[lot_arc(x, y, m)] * sc);
