@@ -34,14 +34,16 @@
 //  duals    every node's potential is the signed sum of arc costs on its path
 //           to the root (pi(x) = c + pi(parent) over an arc x -> parent,
 //           pi(x) = pi(parent) - c over parent -> x): recomputed from the tree
-//           after each pivot by pointer jumping (log2 depth rounds over all
-//           nodes in parallel), so no rounding drift accumulates.
+//           after each pivot by pointer jumping over all nodes in parallel.
+//           A node's jump pointer and partial sum share one 64-bit word, so
+//           every read sees a consistent pair and the jumps need no barrier
+//           between reads and writes (one per pass, about log2 depth passes).
 //
-// One thread block solves one problem and holds its tree in shared memory, 20
-// bytes per node: the int64 potential and the FP64 flow on the node's parent
-// arc, the parent and the arc's direction in 16 bits (an original arc is
-// fixed by its two ends, and points from the source to the sink; an arc to
-// the root is artificial), and a 16-bit jump pointer.  A launch solves
+// One thread block solves one problem and holds its tree in shared memory, 18
+// bytes per node: the potential with the jump pointer (one 64-bit word), the
+// FP64 flow on the node's parent arc, and the parent and the arc's direction
+// in 16 bits (an original arc is fixed by its two ends, and points from the
+// source to the sink; an arc to the root is artificial).  A launch solves
 // `count` problems of one size at once.
 // Every loop has a bound; a tree found inconsistent ends the solve with
 // OT_ERR_NONFINITE instead of looping.
@@ -55,7 +57,6 @@ namespace cyc {
 #define LOT_BT 1024
 #define LOT_BW (LOT_BT / 32)
 #define LOT_MAXM 5120
-#define LOT_JC 4                                             // tree nodes per thread per jumping step
 #define LOT_PRICE_ARCS 16384                                 // arcs priced per step (whole rows)
 #define LOT_PPT (LOT_PRICE_ARCS / LOT_BT)                    // arcs per thread and step
 #define LOT_MAX_ROUNDS 20                                    // pointer-jumping rounds (2^20 > any depth)
@@ -124,7 +125,16 @@ __device__ __forceinline__ double lot_sum(double x, double* s_v) {
     return t;
 }
 
-#define LOT_MARK 0xffffu
+// A node's word: jump pointer in the top 14 bits, potential (|pi| < 2^46) as a
+// 50-bit two's-complement field below it.
+#define LOT_PB 50
+#define LOT_MARK 0x3fff   // jump-pointer value marking a node during a pivot (above any node index)
+
+__device__ __forceinline__ long long lot_pack(int anc, long long pi) {
+    return (long long)(((unsigned long long)anc << LOT_PB) | ((unsigned long long)pi & ((1ull << LOT_PB) - 1)));
+}
+__device__ __forceinline__ int lot_anc(long long w) { return (int)((unsigned long long)w >> LOT_PB); }
+__device__ __forceinline__ long long lot_pi(long long w) { return (long long)((unsigned long long)w << (64 - LOT_PB)) >> (64 - LOT_PB); }
 
 // Original arc between node x and its parent y (one a source, the other a sink).
 __device__ __forceinline__ int lot_arc(int x, int y, int m) {
@@ -133,20 +143,21 @@ __device__ __forceinline__ int lot_arc(int x, int y, int m) {
 
 // One pivot (a single thread).  pu[x] = 2 parent + up (up = 1 when x's parent
 // arc points from x to the parent; the root is its own parent), flow[x] the
-// flow on that arc; anc serves as the mark array here.  Returns 0 or an OT_ERR_*.
-__device__ int lot_pivot(int e, int m, unsigned short* pu, unsigned short* anc, double* flow) {
+// flow on that arc; the jump-pointer fields of the words serve as marks here
+// (every one is the root when a pivot starts).  Returns 0 or an OT_ERR_*.
+__device__ int lot_pivot(int e, int m, unsigned short* pu, long long* word, double* flow) {
     const int V = 2 * m + 1, R = 2 * m;
     const int u = e / m, v = m + (e - (e / m) * m);
     // common ancestor w: mark the path from u to the root, climb from v to a mark
     int x = u;
     for (int s = 0;; ++s) {
         if (s > V) return OT_ERR_NONFINITE;
-        anc[x] = LOT_MARK;
+        word[x] = lot_pack(LOT_MARK, lot_pi(word[x]));
         if (x == R) break;
         x = pu[x] >> 1;
     }
     int w = v;
-    for (int s = 0; anc[w] != LOT_MARK; ++s) {
+    for (int s = 0; lot_anc(word[w]) != LOT_MARK; ++s) {
         if (s > V) return OT_ERR_NONFINITE;
         w = pu[w] >> 1;
     }
@@ -204,10 +215,9 @@ __device__ int lot_pivot(int e, int m, unsigned short* pu, unsigned short* anc, 
 __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_constant__ LotArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
     const int m = A.m, V = 2 * m + 1, R = 2 * m;
-    long long* pi = reinterpret_cast<long long*>(dsm);                    // [V] node potentials (integer costs)
-    double* flow = reinterpret_cast<double*>(pi + V);                     // [V] flow on the parent arc
+    long long* word = reinterpret_cast<long long*>(dsm);                  // [V] jump pointer + potential
+    double* flow = reinterpret_cast<double*>(word + V);                   // [V] flow on the parent arc
     unsigned short* pu = reinterpret_cast<unsigned short*>(flow + V);     // [V] 2 parent + up
-    unsigned short* anc = pu + V;                                         // [V] jump pointers (marks in a pivot)
     __shared__ double s_v[LOT_BW + 1];
     __shared__ long long s_q[LOT_BW + 1];
     __shared__ int s_i[LOT_BW + 1];
@@ -269,21 +279,20 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
 
     // ---- strongly feasible artificial start
     for (int x = tid; x < V; x += LOT_BT) {
-        anc[x] = (unsigned short)R;   // no marks
         if (x == R) {
             pu[x] = (unsigned short)(2 * R);
             flow[x] = 0.0;
-            pi[x] = 0;
+            word[x] = lot_pack(R, 0);
         } else if (x < m) {
             const double al = (double)a[x] * ia;
             const int up = al > 0.0 ? 1 : 0;   // a zero supply hangs below the root with zero flow
             pu[x] = (unsigned short)(2 * R + up);
             flow[x] = al;
-            pi[x] = up ? M : -M;
+            word[x] = lot_pack(R, up ? M : -M);
         } else {
             pu[x] = (unsigned short)(2 * R);   // root -> sink
             flow[x] = (double)b[x - m] * ib;
-            pi[x] = -M;
+            word[x] = lot_pack(R, -M);
         }
     }
     if (tid == 0) s_err = 0;
@@ -308,7 +317,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
 #pragma unroll
             for (int k = 0; k < LOT_PPT; ++k) {
                 if (e < e_end) {
-                    const long long rc = (long long)__float2int_rn(G[e] * sc) - pi[r] + pi[m + j];
+                    const long long rc = (long long)__float2int_rn(G[e] * sc) - lot_pi(word[r]) + lot_pi(word[m + j]);
                     if (rc < best) {
                         best = rc;
                         be = e;
@@ -335,65 +344,50 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             status = OT_ERR_NOT_CONVERGED;
             break;
         }
-        if (tid == 0) s_err = lot_pivot(be, m, pu, anc, flow);
+        if (tid == 0) s_err = lot_pivot(be, m, pu, word, flow);
         __syncthreads();
         if (s_err != OT_OK) {
             status = s_err;
             break;
         }
         ++piv;
-        // potentials by pointer jumping: pi[x] = pi(x) - pi(anc[x]) until anc[x] is the root
+        // potentials by pointer jumping: word[x] = (anc, pi(x) - pi(anc)) until anc is the root
         for (int k = 0; k < npt; ++k) {
             const int x = tid + k * LOT_BT;
             if (x < V) {
                 if (x == R) {
-                    anc[x] = (unsigned short)R;
-                    pi[x] = 0;
+                    word[x] = lot_pack(R, 0);
                 } else {
                     const int y = pu[x] >> 1;
                     const long long c = y == R ? M : (long long)__float2int_rn(G[lot_arc(x, y, m)] * sc);
-                    anc[x] = (unsigned short)y;
-                    pi[x] = (pu[x] & 1) ? c : -c;
+                    word[x] = lot_pack(y, (pu[x] & 1) ? c : -c);
                 }
             }
         }
         __syncthreads();
-        // a round reads (anc[y], pi[y]) of each owned node's y and then writes, LOT_JC owned
-        // nodes at a time: every pair is read either before or after its owner's write, so
-        // each read pair is consistent and pi[x] = pi(x) - pi(anc[x]) holds throughout
+        // passes: each owned node jumps to its pointer's pointer and adds its partial sum.
+        // Only a node's owner writes its word, and every word (one 64-bit shared-memory
+        // access) satisfies the invariant, so reads racing with writes are harmless; a
+        // jump pointer only moves up, and a pass that finds every pointer at the root ends
         int rounds = 0;
-        for (;;) {
-            int any = 0;
-            for (int c0 = 0; c0 < npt; c0 += LOT_JC) {
-                int na[LOT_JC];
-                long long dp[LOT_JC];
-#pragma unroll
-                for (int k = 0; k < LOT_JC; ++k) {
-                    const int x = tid + (c0 + k) * LOT_BT;
-                    na[k] = R;
-                    dp[k] = 0;
-                    if (x < V) {
-                        const int y = anc[x];
-                        if (y != R) {
-                            any = 1;
-                            na[k] = anc[y];
-                            dp[k] = pi[y];
-                        }
+        {
+            volatile long long* vw = word;
+            for (;;) {
+                int any = 0;
+                for (int k = 0; k < npt; ++k) {
+                    const int x = tid + k * LOT_BT;
+                    if (x >= V) break;
+                    const long long w = vw[x];
+                    const int y = lot_anc(w);
+                    if (y != R) {
+                        const long long w2 = vw[y];
+                        vw[x] = lot_pack(lot_anc(w2), lot_pi(w) + lot_pi(w2));
+                        any = 1;
                     }
                 }
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < LOT_JC; ++k) {
-                    const int x = tid + (c0 + k) * LOT_BT;
-                    if (x < V && anc[x] != R) {
-                        pi[x] += dp[k];
-                        anc[x] = na[k];
-                    }
-                }
-                __syncthreads();
+                if (!__syncthreads_or(any)) break;
+                if (++rounds > LOT_MAX_ROUNDS) break;   // uniform; caught below
             }
-            if (!__syncthreads_or(any)) break;
-            if (++rounds > LOT_MAX_ROUNDS) break;   // uniform; caught below
         }
         if (rounds > LOT_MAX_ROUNDS) {
             status = OT_ERR_NONFINITE;
@@ -422,13 +416,13 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             art += flow[x];
         }
     }
-    const long long p0 = pi[0];
+    const long long p0 = lot_pi(word[0]);
     const double unit = ldexp(1.0, -k2);
     double dual = 0.0, l1r = 0.0, l1c = 0.0, l2c = 0.0;
     __syncthreads();
     for (int i = tid; i < m; i += LOT_BT) {
         const double al = (double)a[i] * ia, be2 = (double)b[i] * ib;
-        const double ui = (double)(pi[i] - p0) * unit, vj = (double)(p0 - pi[m + i]) * unit;
+        const double ui = (double)(lot_pi(word[i]) - p0) * unit, vj = (double)(p0 - lot_pi(word[m + i])) * unit;
         A.u[(size_t)p * m + i] = ui;
         A.v[(size_t)p * m + i] = vj;
         dual += al * ui + be2 * vj;
@@ -459,8 +453,9 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     }
 }
 
-size_t lot_smem_bytes(int m) { return (size_t)20 * (2 * (size_t)m + 1) + 16; }
-static_assert(2 * (2 * LOT_MAXM + 1) < 0xffff, "parent and direction fit 16 bits, below the mark");
+size_t lot_smem_bytes(int m) { return (size_t)18 * (2 * (size_t)m + 1) + 16; }
+static_assert(2 * (2 * LOT_MAXM + 1) < 0xffff, "parent and direction fit 16 bits");
+static_assert(2 * LOT_MAXM < LOT_MARK, "node indices fit the 14-bit jump pointer, below the mark");
 
 }  // namespace cyc
 
