@@ -25,7 +25,8 @@ def test_header_declares_the_boundary():
     names = declared_symbols()
     for n in ("ot_fold_cost", "ot_sinkhorn_reduced", "ot_sinkhorn_full", "ot_unfold_plan", "ot_value_and_grad",
               "ot_workspace_bytes", "ot_status_string", "ot_version", "ot_batch_prepare", "ot_batch_fold",
-              "ot_batch_solve", "ot_batch_workspace_bytes"):
+              "ot_batch_solve", "ot_batch_workspace_bytes", "ot_srot_reduced", "ot_srot_workspace_bytes",
+              "ot_lot_reduced", "ot_lot_workspace_bytes"):
         assert n in names
 
 
@@ -44,6 +45,13 @@ def test_host_only_entry_points(libpath):
     assert ctypes.sizeof(cy.ot_problem_desc) == 48
     assert cy.ot_batch_workspace_bytes(0, 8) == 0
     assert cy.ot_batch_workspace_bytes(4, 100) > 0
+    # the reduced LOT's workspace: FP64 row and column sums per problem (256-byte rounded); sizes above
+    # the shared-memory tree's limit (m = 5120) are refused
+    L = cy._lot_lib()
+    assert L.ot_lot_workspace_bytes(3, 100) == (3 * 2 * 100 * 8 + 255) // 256 * 256
+    assert L.ot_lot_workspace_bytes(1, 5120) > 0
+    assert L.ot_lot_workspace_bytes(1, 5121) == 0 and L.ot_lot_workspace_bytes(0, 10) == 0
+    assert cy._srot_lib().ot_srot_workspace_bytes(1024, 9) == 0   # N m above 8192
 
 
 def test_binding_refuses_cpu_tensors(libpath):
@@ -52,6 +60,8 @@ def test_binding_refuses_cpu_tensors(libpath):
     C = torch.zeros((2, 4, 4))
     with pytest.raises(ValueError):
         cy.ot_fold_cost(cy.OT_MIN, 4, 2, C_base=C, G=torch.zeros((4, 4)), kstar=torch.zeros((4, 4), dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        cy.ot_lot_reduced(4, 2, torch.ones(4), torch.ones(4), torch.zeros((4, 4)))
 
 
 def test_struct_layouts_match_header():
