@@ -55,6 +55,13 @@ entries per row): the reduced alternating minimisation against the same
 method on the full problem (N = 1 on the assembled 4096 x 4096 cost), both to
 full-scale row L1 <= 1e-6; the FP64 oracle's sweeps timed on a sample.
 
+``--workload lot``: C-LOT (Algorithm 1) in the paper's synthetic setting, the
+rows of Table 1's cyclic network simplex: d in {5000, 10000}, N in {2, 5, 10,
+25, 50}, 20 instances per row solved in one launch (min-fold, the small LOT by
+the GPU network simplex, compact unfold); the headline row is d = 10000,
+N = 10 (m = 1000).  One instance is checked against the oracle's LP value and
+timed on the host (HiGHS) as the CPU baseline.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle
 on a bounded sample of the same workload instead.
 """
