@@ -213,8 +213,3 @@ def primal_value_reduced(T_blocks, C_base, lam) -> dict:
     reg = float(entropy_phi(T_blocks, lam).sum())
     return {"value": N * (tc + reg), "transport_cost": N * tc}
 
-
-def reduced_plan_sums(T_blocks):
-    """S = sum_k T_k (Sec. 5.2's auxiliary variable) and its row / column sums."""
-    S = T_blocks.sum(axis=0)
-    return S, S.sum(axis=1), S.sum(axis=0)

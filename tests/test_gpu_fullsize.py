@@ -11,6 +11,8 @@ size:
 * polar (n = 65536, N = 16): the reduced path and the full on-the-fly solve
   stop after the same number of iterations (tiled iterates), the full
   potentials equal the tiled reduced ones, sampled rows' marginals in FP64;
+  the value, transport cost and envelope gradients of the value-and-gradient
+  call against the oracle's reduced solve at m = 4096;
 * the paper's synthetic setting at d = 10000, N = 2: the same properties on
   the stored-cost paths.
 """
@@ -21,6 +23,7 @@ import pytest
 import torch
 
 from paper_2311_13147_gb300 import inputs as I
+from oracle import grad as OG
 from oracle import sinkhorn as OS
 
 pytestmark = pytest.mark.gpu
@@ -182,6 +185,27 @@ def test_polar_full_size(cy):
         row = np.exp((fg[R] + gg - c) / eps).sum()
         err = max(err, abs(row - an[R]) / an[R])
     assert err <= 1e-3   # per-row relative error of a state with full-scale L1 <= 1e-6 on 65536 rows
+    # the value-and-gradient call of the workload, against the oracle's reduced solve at m = 4096
+    # (same tolerance, hence the same iteration) and its envelope gradients from the same state
+    xd = dev(x32)
+    d_a, d_b = torch.empty(m, device="cuda"), torch.empty(m, device="cuda")
+    d_x, d_y = torch.empty((m, 2), device="cuda"), torch.empty((m, 2), device="cuda")
+    vout = cy.ot_value_and_grad(m, N, dev(p.a_base), dev(p.b_base), x=xd, y=xd, w=w, z=z, eps=eps,
+                                d_a=d_a, d_b=d_b, d_x=d_x, d_y=d_y)
+    rv = cy.read_result(vout)
+    assert rv["status"] == cy.OT_OK
+    x64 = x32.astype(np.float64)
+    C64 = OG.cost_from_points(x64, x64, N)
+    env = OG.envelope_grad(p.a_base, p.b_base, C64, eps, tol=tol, x=x64, y=x64)
+    assert abs(env["iters"] - r["iters"]) <= 2, (env["iters"], r["iters"])
+    v = OS.primal_value_reduced(OS.unfold_erot(env["w"], env["z"], C64, eps), C64, eps)
+    del C64
+    assert rv["value"] == pytest.approx(v["value"], rel=1e-5)
+    assert rv["transport_cost"] == pytest.approx(v["transport_cost"], rel=1e-5)
+    rel = lambda g, ref: np.abs(g - ref).max() / np.abs(ref).max()
+    assert rel(d_a.cpu().numpy(), env["d_a"]) < 5e-4
+    assert rel(d_b.cpu().numpy(), env["d_b"]) < 5e-4
+    assert rel((d_x + d_y).cpu().numpy(), env["d_x"] + env["d_y"]) < 5e-4
 
 
 def test_paper_setting_d10000_n2(cy):

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances, each derived from the arithmetic on both sides:
 * LOT min-fold, kstar and the unfold index map: bit-exact.
 * EROT objective (regularised value and transport cost): 1e-5 relative.
 * Marginals: the oracle evaluates the GPU's potentials in FP64; the full-scale
@@ -414,3 +414,95 @@ def test_full_streaming_route_warm_start(cy):
                                        g=g.clone())
     r2 = cy.read_result(out2)
     assert r2["status"] == cy.OT_OK and r2["iters"] <= 2
+
+
+# ------------------------------------------------------------------ reported marginal norms and objective
+
+def _full_plan_norms(w, z, p):
+    """The paper's marginal errors from their definition on the assembled n x n plan (Lemma 1):
+    row L1 sum |T 1 - a|, column L1 and column L2 ||T^T 1 - b||_2 (Sec. 7.1), unit-mass a, b."""
+    Tb = OS.unfold_erot(np.asarray(w, np.float64), np.asarray(z, np.float64), p.C_base.astype(np.float64), p.eps)
+    T = OR.assemble_block_circulant(Tb)
+    a = np.tile(OS.normalise(p.a_base), p.N) / p.N
+    b = np.tile(OS.normalise(p.b_base), p.N) / p.N
+    e = OR.marginal_errors(T, a, b)
+    v = OS.primal_value_reduced(Tb, p.C_base.astype(np.float64), p.eps)
+    return e, v
+
+
+NORM_CASES = [("sector", 130, 5, 0.01), ("grid", 32, 4, 0.01), ("grid", 64, 4, 0.01), ("paper", 200, 20, 0.0)]
+
+
+def _norm_problem(kind, s, N, frac):
+    if kind == "sector":
+        return I.sector_problem(s, N, seed=3, eps_frac=frac)
+    if kind == "grid":
+        return I.image_grid_problem(side=s, seed=1, eps_frac=frac)
+    return I.paper_synthetic_problem(s, N, seed=1)
+
+
+@pytest.mark.parametrize("kind,s,N,frac", NORM_CASES)
+def test_reported_norms_and_value_vs_full_plan(cy, kind, s, N, frac):
+    """marg_l1, marg_l1_col and marg_l2_col of ot_value_and_grad against the oracle's FP64 norms
+    of the same potentials, evaluated on the assembled n x n plan.
+
+    The GPU forms every plan entry with ex2.approx (relative error <= 2^-22 ~ 2.4e-7) from FP32
+    arguments and sums them in FP32 before the FP64 accumulation (a few roundings of 6e-8), so
+    each row or column sum carries a relative error of at most ~4e-7 of its mass; summed over a
+    unit-mass plan that bounds every reported L1 norm (and the L2 norm, which is below the L1)
+    by 5e-7 absolute.
+    (1) The converged state (norms ~1e-7, i.e. at that floor): within 5e-7 + 1% relative.
+    (2) The converged potentials with a seeded perturbation of 0.02 eps (norms ~1e-2): within
+        5e-7 + 1e-4 relative, where any formula slip (scale N, sqrt, row/column swap) is visible;
+        value and transport cost of that plan within 1e-5 relative.
+    """
+    p = _norm_problem(kind, s, N, frac)
+    Cb, G, w, z, res = _solve_reduced(cy, p, 1e-6, max_iter=100000)
+    assert res["status"] == cy.OT_OK
+    a, b = dev(p.a_base), dev(p.b_base)
+    rng = np.random.default_rng(11)
+    wz = [(host(w), host(z))]
+    wz.append((wz[0][0] + 0.02 * p.eps * rng.standard_normal(p.m), wz[0][1] + 0.02 * p.eps * rng.standard_normal(p.m)))
+    for case, (wh, zh) in enumerate(wz):
+        out = cy.ot_value_and_grad(p.m, p.N, a, b, C_base=Cb, w=dev(wh), z=dev(zh), eps=p.eps)
+        r = cy.read_result(out)
+        assert r["status"] == cy.OT_OK
+        e, v = _full_plan_norms(wh, zh, p)
+        rt = 1e-2 if case == 0 else 1e-4
+        assert abs(r["marg_l1"] - e["row_l1"]) <= 5e-7 + rt * e["row_l1"], (case, r["marg_l1"], e["row_l1"])
+        assert abs(r["marg_l1_col"] - e["col_l1"]) <= 5e-7 + rt * e["col_l1"], (case, r["marg_l1_col"], e["col_l1"])
+        assert abs(r["marg_l2_col"] - e["col_l2"]) <= 5e-7 + rt * e["col_l2"], (case, r["marg_l2_col"], e["col_l2"])
+        assert r["value"] == pytest.approx(v["value"], rel=1e-5)
+        assert r["transport_cost"] == pytest.approx(v["transport_cost"], rel=1e-5)
+    # the solver's own stopping measure is the same row L1 of the returned state
+    assert abs(res["marg_l1"] - _full_plan_norms(*wz[0], p)[0]["row_l1"]) <= 5e-7 + 1e-2 * res["marg_l1"]
+
+
+# ------------------------------------------------------------------ the paper's synthetic setting (Sec. 7.1, App. D)
+
+@pytest.mark.parametrize("m,N", [(1000, 10), (200, 50), (4100, 10)])
+def test_paper_synthetic_erot_vs_oracle(cy, m, N):
+    """Cyclic Sinkhorn on the paper's synthetic inputs: cost blocks ~ N(3, 5^2) shifted to be
+    non-negative, marginal blocks ~ U[0, 1) (near-zero entries included), lambda = 0.5.  m = 4100
+    (d = 41000) takes the streaming route with ragged rows (4100 columns: not a multiple of the
+    row chunk).  Against the oracle at the same tolerance: iterations, FP64 marginals of the GPU
+    potentials, value and transport cost (1e-5 relative)."""
+    p = I.paper_synthetic_problem(m, N, seed=0)
+    tol = 1e-6
+    Cb, G, w, z, res = _solve_reduced(cy, p, tol, max_iter=100000)
+    assert res["status"] == cy.OT_OK, res
+    assert res["marg_l1"] <= tol
+    if m > 4096:
+        assert res["variant"] == "stream"
+    orc = OS.cyclic_sinkhorn(p.a_base, p.b_base, p.C_base, p.eps, tol=tol)
+    assert abs(res["iters"] - orc["iters"]) <= 0.03 * orc["iters"] + 2, (res["iters"], orc["iters"])
+    wg, zg = host(w), host(z)
+    rl1, cl1 = fp64_row_col_errors(wg, zg, p.C_base, p.a_base, p.b_base, p.eps)
+    assert rl1 <= tol + (1e-6 if m > 4096 else 2e-7) and cl1 <= 1e-6, (rl1, cl1)
+    out = cy.ot_value_and_grad(m, N, dev(p.a_base), dev(p.b_base), C_base=Cb, w=w, z=z, eps=p.eps)
+    r = cy.read_result(out)
+    v = OS.primal_value_reduced(OS.unfold_erot(orc["w"], orc["z"], p.C_base.astype(np.float64), p.eps),
+                                p.C_base.astype(np.float64), p.eps)
+    assert r["value"] == pytest.approx(v["value"], rel=1e-5)
+    assert r["transport_cost"] == pytest.approx(v["transport_cost"], rel=1e-5)
+
