@@ -108,13 +108,17 @@ typedef struct {
                                        first grid barrier, [3] column phase done.
                                        bit 2 (OT_DEBUG_NO_CLUSTER): do not use the
                                        one-barrier-per-sweep (bulk reduce-add) solver;
-                                       use the two-barrier one (comparison runs).        */
+                                       use the two-barrier one (comparison runs).
+                                       bit 3 (OT_DEBUG_RING): use the ring solver
+                                       (per-thread copy ring, FP32 sweep) for every
+                                       stored cost it takes (comparison runs).          */
     int stop_norm;                  /* OT_STOP_L1_FULL (default) or OT_STOP_L2_ROW          */
 } ot_options;
 
 #define OT_DEBUG_WITHHOLD_ARRIVAL 1
 #define OT_DEBUG_TRACE            2
 #define OT_DEBUG_NO_CLUSTER       4
+#define OT_DEBUG_RING             8
 
 /* Device-written outcome of one solve.  64 bytes, naturally aligned. */
 typedef struct {

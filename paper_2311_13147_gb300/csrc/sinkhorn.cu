@@ -160,6 +160,7 @@ __device__ __forceinline__ void store_row(const SkArgs& A, const RowState& S, in
 #define OT_VARIANT_BULK 1.0
 #define OT_VARIANT_FUSED 2.0
 #define OT_VARIANT_TWOPASS 3.0
+#define OT_VARIANT_RING 7.0
 
 __device__ void write_result(const SkArgs& A, int iters, int status, double l1, double variant) {
     if (threadIdx.x == 0) {
@@ -994,6 +995,552 @@ __global__ void __launch_bounds__(OT_BLOCK, 1) sk_bulk_kernel(SkArgs A, int nsta
 }
 
 // ---------------------------------------------------------------------------
+// Ring kernel: per-thread asynchronous-copy ring, FP32 sweep, one grid barrier
+// ---------------------------------------------------------------------------
+//
+// The same single-read sweep as the kernels above (one cost read and one exp2
+// per entry, row sums around the previous row potential, column contributions
+// u_i * e_ij from the row pass's exponentials), laid out for 512 threads:
+//
+// * Cost bands reach shared memory by per-thread 16-byte asynchronous copies
+//   (cp.async.cg, L2 only): each thread copies exactly the float4 slots it
+//   later reads, so a band needs no block barrier to become visible -- each
+//   thread waits for its own copy groups (cp.async.wait_group).  S stages are
+//   in flight per block; a stage is refilled as soon as its thread has turned
+//   the band's costs into exponentials.  The ring runs across sweeps (the next
+//   sweep's first bands load during the column exchange).  When all of a
+//   block's rows fit, they are copied once and stay resident.
+// * Every arithmetic step of a sweep is FP32 (this GPU's FP64 pipe, and its
+//   FP32 <-> FP64 conversions, are far slower than FP32): potentials are
+//   (hi, lo) pairs updated by error-free transformations, and the column
+//   partials are converted to FP64 bit patterns by integer operations.
+// * The column sums are added at L2 in FP64 by one bulk reduce-add per block
+//   (cp.reduce.async.bulk .add.f64) into a triple-buffered vector, followed by
+//   ONE grid barrier; then every block reads the vector and updates the
+//   potentials of all columns in registers (identical arithmetic everywhere).
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// x >= 0 (FP32) -> the same value as an FP64 bit pattern, by integer operations:
+// exact for normal x; zero and the flush-to-zero range give 0, Inf and NaN give NaN.
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+    const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+    const unsigned e = b >> 23;
+    unsigned long long d = ((unsigned long long)b << 29) + (896ull << 52);
+    d = (e == 0u) ? 0ull : d;
+    d = (e == 255u) ? 0x7ff8000000000000ull : d;
+    return __longlong_as_double((long long)d);
+}
+
+// x >= 0 (FP64) -> nearest FP32 (ties away from zero) by integer operations; below the
+// FP32 normal range -> 0, above -> Inf, Inf and NaN -> NaN.
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+    const unsigned long long d = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    const unsigned e = (unsigned)(d >> 52);
+    const unsigned r = (unsigned)((d - (896ull << 52) + (1ull << 28)) >> 29);
+    float f = __uint_as_float(r);
+    f = (e < 897u) ? 0.f : f;
+    f = (e > 1150u) ? __uint_as_float(0x7f800000u) : f;
+    f = (e == 0x7ffu) ? __uint_as_float(0x7fc00000u) : f;
+    return f;
+}
+
+// (hi, lo) = a - d exactly (two-difference).
+__device__ __forceinline__ void two_diff(float a, float d, float& hi, float& lo) {
+    const float s = a - d;
+    const float bb = s - a;
+    lo = (a - (s - bb)) + (-d - bb);
+    hi = s;
+}
+
+// Shared-memory row state of the ring kernel (rows the block owns).
+struct RingRows {
+    float* hi;      // [2][rows_max]  hi part of the row potential (log2 units)
+    float* lo;      // [2][rows_max]  lo part
+    float* fr;      // [2][rows_max]  2^lo
+    float* alpha;   // [rows_max]     normalised row marginal
+};
+
+// Issue the copies of band `band` of this block into ring stage `st` (this thread's slots).
+template <int NT, int CPT, int R>
+__device__ __forceinline__ void ring_issue(const SkArgs& A, float* ring, int st, int r_beg, int r_end, int band) {
+    const int rb = r_beg + band * R;
+    const int nr = min(R, r_end - rb);
+    float* dst = ring + (size_t)st * R * A.Ncol;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r < nr) {
+#pragma unroll
+            for (int q = 0; q < CPT / 4; ++q) {
+                const int j4 = threadIdx.x + q * NT;
+                if (4 * j4 < A.Ncol) cp_async16(dst + (size_t)r * A.Ncol + 4 * j4, A.C + (long long)(rb + r) * A.ld + 4 * j4);
+            }
+        }
+    }
+}
+
+// One band of up to R rows, from ring stage `sb` (row stride rstride floats) or, with
+// GSRC, straight from the cost rows in global memory.  Exponents from the thread's own
+// slots, exp2, row sums (one block barrier), factors u_r = alpha_r / S_r for every
+// thread, new row potentials and the row L1 terms (warp 0).  The callback `refill`
+// runs once the stage's contents are in registers.  Returns true when some row sum
+// left the safe range (the same answer in every thread).
+template <int NT, int CPT, int R, bool SAFE, bool GSRC, typename Refill>
+__device__ __forceinline__ bool ring_band(const SkArgs& A, const RingRows& RS, const float* sb, long long rstride,
+                                          int rb, int lb, int nr,
+                                          int cur, int nxt, const float (&ghi)[CPT], const float (&cf)[CPT],
+                                          float (&e)[R][CPT], float (&u)[R], float& l1, float (*s_red)[NT / 32],
+                                          Refill refill) {
+    constexpr int NW = NT / 32;
+    constexpr int NV = CPT / 4;
+    constexpr int LOGR = (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int rm = A.rows_max;
+    const int my_row = (lane >> (5 - LOGR)) & (R - 1);
+    const bool writer = (lane & ((32 >> LOGR) - 1)) == 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool rv = r < nr;
+        const float F = (SAFE || !rv) ? 0.f : RS.hi[cur * rm + lb + r];
+        const float4* srow = reinterpret_cast<const float4*>(sb + (rv ? r : 0) * rstride);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const int j4 = tid + q * NT;
+            if (rv && 4 * j4 < A.Ncol) {
+                const float4 c = GSRC ? __ldg(srow + j4) : srow[j4];
+                e[r][4 * q + 0] = fmaf(c.x, -A.kappa, ghi[4 * q + 0]) + F;
+                e[r][4 * q + 1] = fmaf(c.y, -A.kappa, ghi[4 * q + 1]) + F;
+                e[r][4 * q + 2] = fmaf(c.z, -A.kappa, ghi[4 * q + 2]) + F;
+                e[r][4 * q + 3] = fmaf(c.w, -A.kappa, ghi[4 * q + 3]) + F;
+            } else {
+                e[r][4 * q + 0] = e[r][4 * q + 1] = e[r][4 * q + 2] = e[r][4 * q + 3] = -INFINITY;
+            }
+        }
+    }
+    refill();   // the stage's costs now live in registers
+    float Fsafe = 0.f;
+    if (SAFE) {
+        float mx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            mx[r] = e[r][0];
+#pragma unroll
+            for (int q = 1; q < CPT; ++q) mx[r] = fmaxf(mx[r], e[r][q]);
+        }
+        const float m = warp_reduce_rows<R, true>(mx, lane);
+        if (writer) s_red[my_row][wid] = m;
+        __syncthreads();
+        float mm = -INFINITY;
+        if (lane < nr) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) mm = fmaxf(mm, s_red[lane][w]);
+        }
+        Fsafe = (mm > -INFINITY) ? -mm : 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float F = __shfl_sync(0xffffffffu, Fsafe, r);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) e[r][q] += F;
+        }
+        __syncthreads();   // s_red is reused for the sums below
+    }
+    float ps[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            e[r][q] = ex2(e[r][q]);
+            s = fmaf(e[r][q], cf[q], s);
+        }
+        ps[r] = s;
+    }
+    const float wsum = warp_reduce_rows<R, false>(ps, lane);
+    if (writer) s_red[my_row][wid] = wsum;
+    __syncthreads();
+    float S = 1.f, alpha = 0.f;
+    if (lane < nr) {
+        const float4* rr = reinterpret_cast<const float4*>(s_red[lane]);
+        float4 acc4 = rr[0];
+#pragma unroll
+        for (int w = 1; w < NW / 4; ++w) {
+            const float4 p = rr[w];
+            acc4.x += p.x; acc4.y += p.y; acc4.z += p.z; acc4.w += p.w;
+        }
+        S = (acc4.x + acc4.y) + (acc4.z + acc4.w);
+        alpha = RS.alpha[lb + lane];
+    }
+    const bool ok = (lane >= nr) || sum_ok(S);
+    const float ul = (lane < nr) ? __fdividef(alpha, S) : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = __shfl_sync(0xffffffffu, ul, r);
+    const bool bad = !__all_sync(0xffffffffu, ok);
+    if (wid == 0 && lane < nr) {
+        const int li = lb + lane;
+        const float d = lg2(__fdividef(S, alpha));
+        float base;
+        if (!SAFE) {
+            // L1 term of the current state: |S * 2^lo - alpha|; a row out of range counts as unconverged
+            l1 += ok ? fabsf(fmaf(S, RS.fr[cur * rm + li] - 1.0f, S - alpha)) : 1e30f;
+            base = RS.hi[cur * rm + li];
+        } else {
+            base = Fsafe;
+        }
+        if (ok) {
+            float h, l;
+            two_diff(base, d, h, l);
+            const float f = ex2(l);
+            RS.hi[nxt * rm + li] = h;
+            RS.lo[nxt * rm + li] = l;
+            RS.fr[nxt * rm + li] = f;
+            A.fhi[nxt * A.M + rb + lane] = h;
+            A.frf[nxt * A.M + rb + lane] = f;
+        }
+    }
+    return bad;
+}
+
+// Column potential from scratch with an explicit max shift over the column (rare: the
+// column sum left the safe range).  Whole block; every thread gets (hi, lo).
+template <int NT>
+__device__ void ring_column_fallback(const SkArgs& A, int j, int nb, float beta, float* s_redf, float& hi,
+                                     float& lo) {
+    constexpr int NW = NT / 32;
+    const float* fh = A.fhi + nb * A.M;
+    const float* fr = A.frf + nb * A.M;
+    float mx = -INFINITY;
+    for (int i = threadIdx.x; i < A.M; i += NT) mx = fmaxf(mx, fmaf(A.C[(long long)i * A.ld + j], -A.kappa, fh[i]));
+    mx = warp_max(mx);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_redf[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    float m2 = s_redf[0];
+    for (int w = 1; w < NW; ++w) m2 = fmaxf(m2, s_redf[w]);
+    __syncthreads();
+    float s = 0.f;
+    for (int i = threadIdx.x; i < A.M; i += NT) s += ex2(fmaf(A.C[(long long)i * A.ld + j], -A.kappa, fh[i]) - m2) * fr[i];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) s_redf[threadIdx.x >> 5] = s;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < NW; ++w) tot += s_redf[w];
+    __syncthreads();
+    if (!(tot > 0.f) || !(m2 > -INFINITY) || !(beta > 0.f)) {
+        if (threadIdx.x == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
+        hi = 0.f;
+        lo = 0.f;
+        return;
+    }
+    // gamma = log2 beta - m2 - log2 tot
+    two_diff(lg2(beta), m2, hi, lo);
+    df_sub(hi, lo, lg2(tot));
+}
+
+template <int NT, int CPT, int R, int S>
+__global__ void __launch_bounds__(NT, 1) sk_ring_kernel(SkArgs A) {
+    constexpr int NW = NT / 32;
+    constexpr int NV = CPT / 4;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(16) float s_red[2][R][NW];
+    __shared__ float s_redf[NW];
+    __shared__ int s_nfix;
+    __shared__ int s_fix[64];
+    __shared__ float s_fixv[64][2];
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int B = blockIdx.x, G = gridDim.x;
+    const int Nc = A.Ncol;
+    const int r_beg = (int)((long long)A.M * B / G), r_end = (int)((long long)A.M * (B + 1) / G);
+    const int o_beg = (int)((long long)Nc * B / G), o_end = (int)((long long)Nc * (B + 1) / G);
+    const int z_beg = (int)((long long)A.vstride * B / G), z_end = (int)((long long)A.vstride * (B + 1) / G);
+    const int nbands = (r_end - r_beg + R - 1) / R;
+    const bool resident = A.resident != 0;
+    const int lsl = NV * 4 * NT;   // the L1 slot of the column-sum vector
+
+    // dynamic shared memory: [ring][partials (4 NT + 2 doubles)][row state]
+    float* ring = reinterpret_cast<float*>(dsm);
+    const int nstage = resident ? nbands : S;
+    unsigned char* p = dsm + align256_hd((size_t)nstage * R * Nc * sizeof(float));
+    double* s_part = reinterpret_cast<double*>(p);
+    p += align256_hd((size_t)(4 * NT + 2) * sizeof(double));
+    RingRows RS;
+    RS.hi = reinterpret_cast<float*>(p);
+    RS.lo = RS.hi + 2 * A.rows_max;
+    RS.fr = RS.lo + 2 * A.rows_max;
+    RS.alpha = RS.fr + 2 * A.rows_max;
+    unsigned epoch = 0;
+
+    // ---- first copies: every band (resident) or the first S bands of the ring
+    long long issued = 0;
+    if (nbands > 0) {
+        if (resident) {
+            for (int b = 0; b < nbands; ++b) ring_issue<NT, CPT, R>(A, ring, b, r_beg, r_end, b);
+            cp_async_commit();
+        } else {
+            for (int s = 0; s < S; ++s) {
+                ring_issue<NT, CPT, R>(A, ring, s, r_beg, r_end, s % nbands);
+                cp_async_commit();
+            }
+            issued = S;
+        }
+    }
+    long long consumed = 0;
+
+    __shared__ double s_dred[NW];
+    double sa = 0.0, sb = 0.0;   // marginal sums (FP64, once per solve)
+    int badm = 0;
+    for (int i = tid; i < A.M; i += NT) { const float v = A.a[i]; badm |= !(v > 0.f && v < INFINITY); sa += v; }
+    for (int j = tid; j < Nc; j += NT) { const float v = A.b[j]; badm |= !(v > 0.f && v < INFINITY); sb += v; }
+    sa = warp_sum(sa);
+    sb = warp_sum(sb);
+    if (lane == 0) s_dred[wid] = sa;
+    __syncthreads();
+    double tsa = 0.0;
+    for (int w = 0; w < NW; ++w) tsa += s_dred[w];
+    __syncthreads();
+    if (lane == 0) s_dred[wid] = sb;
+    __syncthreads();
+    double tsb = 0.0;
+    for (int w = 0; w < NW; ++w) tsb += s_dred[w];
+    const bool args_ok = __syncthreads_or(badm) == 0;
+    const double inv_sa = 1.0 / tsa, inv_sb = 1.0 / tsb;
+    for (int li = tid; li < r_end - r_beg; li += NT) RS.alpha[li] = (float)((double)A.a[r_beg + li] * inv_sa);
+    if (tid == 0) s_nfix = 0;
+    // column state in registers: potentials (hi, lo), 2^lo, normalised column marginal
+    float ghi[CPT], glo[CPT], cf[CPT], beta[CPT];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = 4 * (tid + q * NT) + v;
+            float hi = 0.f, lo = 0.f, bt = 1.f;
+            if (j < Nc) {
+                const double g0 = A.warm ? A.g_out[j] / A.unit : 0.0;
+                split_f64(g0, hi, lo);
+                bt = (float)((double)A.b[j] * inv_sb);
+            }
+            ghi[4 * q + v] = hi;
+            glo[4 * q + v] = lo;
+            cf[4 * q + v] = (j < Nc) ? ex2(lo) : 0.f;
+            beta[4 * q + v] = bt;
+        }
+    }
+    const float tolf = (float)A.tol;
+    bool go = args_ok;
+    if (go && (A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
+        withhold_arrival(A.ctrl, A.timeout_ns);
+        go = false;
+    } else if (go) {
+        go = grid_sync(A.ctrl, G, A.timeout_ns, epoch);
+    }
+
+    for (int t = 1; go; ++t) {
+        const int cur = (t - 1) & 1, nxt = cur ^ 1;
+        double* vec = A.acc + (size_t)(t % 3) * A.vstride;
+        double* vzero = A.acc + (size_t)((t + 2) % 3) * A.vstride;
+        trace_mark(A, t, 0);
+        float acc[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
+        float l1 = 0.f;
+        float e[R][CPT];
+        if (resident && t == 1) cp_async_wait_all();
+        for (int b = 0; b < nbands; ++b) {
+            const int rb = r_beg + b * R;
+            const int lb = b * R;
+            const int nr = min(R, r_end - rb);
+            int st = b;
+            if (!resident) {
+                cp_async_wait<S - 1>();
+                st = (int)(consumed % S);
+            }
+            const float* sbase = ring + (size_t)st * R * Nc;
+            auto refill = [&]() {
+                if (!resident) {
+                    ring_issue<NT, CPT, R>(A, ring, st, r_beg, r_end, (int)(issued % nbands));
+                    cp_async_commit();
+                }
+            };
+            auto none = []() {};
+            float u[R];
+            bool bad;
+            if (t == 1)
+                bad = ring_band<NT, CPT, R, true, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, ghi, cf, e, u, l1,
+                                                         s_red[b & 1], refill);
+            else
+                bad = ring_band<NT, CPT, R, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, ghi, cf, e, u, l1,
+                                                          s_red[b & 1], refill);
+            if (!resident) { ++consumed; ++issued; }
+            if (bad) {   // uniform over the block: redo the band max-shifted, its costs re-read from global memory
+                __syncthreads();   // (the ring stage may already hold the next band)
+                float dummy = 0.f;
+                if (ring_band<NT, CPT, R, true, true>(A, RS, A.C + (long long)rb * A.ld, A.ld, rb, lb, nr, cur, nxt, ghi,
+                                                      cf, e, u, dummy, s_red[b & 1], none))
+                    if (tid == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < nr) {
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) acc[q] = fmaf(u[r], e[r][q], acc[q]);
+                }
+            }
+        }
+        trace_mark(A, t, 4);
+        // ---- column partials (FP64 bit patterns) and the L1 term: one bulk reduce-add per chunk of 4 NT columns
+        if (wid == 0) l1 = warp_sum(l1);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            if (q > 0) {
+                if (tid == 0) bulk_wait_read();   // the previous chunk has left shared memory
+                __syncthreads();
+            }
+            double2* dst = reinterpret_cast<double2*>(s_part + 4 * tid);
+            dst[0] = make_double2(f32_to_f64_bits(acc[4 * q]), f32_to_f64_bits(acc[4 * q + 1]));
+            dst[1] = make_double2(f32_to_f64_bits(acc[4 * q + 2]), f32_to_f64_bits(acc[4 * q + 3]));
+            const bool last = q == NV - 1;
+            if (last && tid == 0) {
+                s_part[4 * NT] = f32_to_f64_bits(l1);
+                s_part[4 * NT + 1] = 0.0;
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                if (q == 0) fence_proxy_async_global();   // the slice clears of earlier sweeps precede these adds
+                bulk_reduce_add_f64(vec + 4 * NT * q, s_part, (unsigned)((4 * NT + (last ? 2 : 0)) * sizeof(double)));
+            }
+        }
+        if (tid == 0) {
+            bulk_wait_all();
+            fence_proxy_async_global();
+        }
+        trace_mark(A, t, 1);
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
+        trace_mark(A, t, 2);
+
+        // ---- column sums of this thread's columns and the L1 of the state after t - 1 iterations
+        double2 v01[NV], v23[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const double2* src = reinterpret_cast<const double2*>(vec + 4 * (tid + q * NT));
+            v01[q] = __ldcg(src);
+            v23[q] = __ldcg(src + 1);
+        }
+        const double L1d = __ldcg(vec + lsl);
+        const float L1 = f64_to_f32_bits(L1d);
+        trace_mark(A, t, 5);
+        int stt = -1;
+        if (t - 1 >= 1) {
+            if (L1 != L1) stt = OT_ERR_NONFINITE;
+            else if ((t - 1) % A.check_every == 0 && L1 <= tolf) stt = OT_OK;
+            else if (t - 1 >= A.max_iter) stt = OT_ERR_NOT_CONVERGED;
+        }
+        if (stt >= 0) {
+            for (int li = tid; li < r_end - r_beg; li += NT)
+                A.f_out[r_beg + li] =
+                    ((double)RS.hi[cur * A.rows_max + li] + (double)RS.lo[cur * A.rows_max + li]) * A.unit + A.f_shift;
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int j = 4 * (tid + q * NT) + v;
+                    if (j >= o_beg && j < o_end) A.g_out[j] = ((double)ghi[4 * q + v] + (double)glo[4 * q + v]) * A.unit;
+                }
+            if (B == 0 && tid == 0) {
+                A.res->iters = t - 1;
+                A.res->status = stt;
+                A.res->marg_l1 = L1d;
+                A.res->marg_l2_col = -1.0;
+                A.res->value = 0.0;
+                A.res->transport_cost = 0.0;
+                A.res->marg_l1_col = -1.0;
+                A.res->reserved[0] = 0.0;
+                A.res->reserved[1] = OT_VARIANT_RING;
+            }
+            break;
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const float Av[4] = {f64_to_f32_bits(v01[q].x), f64_to_f32_bits(v01[q].y), f64_to_f32_bits(v23[q].x),
+                                 f64_to_f32_bits(v23[q].y)};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int k = 4 * q + v;
+                const int j = 4 * (tid + q * NT) + v;
+                if (j < Nc) {
+                    const float Rj = Av[v] * cf[k];   // column sum of the plan after the row update
+                    if (Rj != Rj) {
+                        set_status(A.ctrl, OT_ERR_NONFINITE);
+                    } else if (Rj > 1e-30f && Rj < 1e30f) {
+                        df_sub(ghi[k], glo[k], lg2(__fdividef(Rj, beta[k])));
+                        cf[k] = ex2(glo[k]);
+                    } else {
+                        const int k2 = atomicAdd(&s_nfix, 1);
+                        if (k2 < 64) s_fix[k2] = j;
+                        else set_status(A.ctrl, OT_ERR_NONFINITE);
+                    }
+                }
+            }
+        }
+        trace_mark(A, t, 6);
+        // clear this block's slice of the vector read in sweep t-1 (next written in sweep t+2)
+        if (z_beg + tid < z_end) {
+            for (int k = z_beg + tid; k < z_end; k += NT) vzero[k] = 0.0;
+            fence_proxy_async_global();
+        }
+        __syncthreads();
+        const int nfix = min(s_nfix, 64);
+        if (nfix > 0) {   // rare: column sums out of range, recomputed with an explicit max by every block
+            for (int k = 0; k < nfix; ++k) {
+                const int j = s_fix[k];
+                float h, l;
+                ring_column_fallback<NT>(A, j, nxt, (float)((double)A.b[j] * inv_sb), s_redf, h, l);
+                if (tid == 0) { s_fixv[k][0] = h; s_fixv[k][1] = l; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int j = 4 * (tid + q * NT) + v;
+                    for (int k = 0; k < nfix; ++k)
+                        if (s_fix[k] == j) {
+                            ghi[4 * q + v] = s_fixv[k][0];
+                            glo[4 * q + v] = s_fixv[k][1];
+                            cf[4 * q + v] = ex2(s_fixv[k][1]);
+                        }
+                }
+            __syncthreads();
+            if (tid == 0) s_nfix = 0;
+            __syncthreads();
+        }
+        trace_mark(A, t, 3);
+    }
+    if (!args_ok) {
+        if (B == 0 && tid == 0) {
+            A.res->iters = 0;
+            A.res->status = OT_ERR_ARG;
+            A.res->marg_l1 = -1.0;
+            A.res->reserved[1] = OT_VARIANT_RING;
+        }
+    } else if (!go) {
+        fail_exit(A);
+    }
+    cp_async_wait_all();   // no copy may still target this block's shared memory when it exits
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Two-pass kernel (any width; stored or on-the-fly cost)
 // ---------------------------------------------------------------------------
 
@@ -1268,7 +1815,7 @@ static WsLayout ws_layout(int M, int Ncol, int grid, bool fused) {
     L.part = o; o = align256_hd(o + (fused ? sizeof(float) * (size_t)grid * L.pstride : 0));
     L.l1part = o; o = align256_hd(o + sizeof(double) * (size_t)grid);
     L.queue = o; o = align256_hd(o + sizeof(unsigned) * 2);
-    L.vstride = ((Ncol + 2) + 31) & ~31;
+    L.vstride = ((((Ncol + 2047) & ~2047) + 2) + 31) & ~31;   // whole 4 NT-column chunks + the L1 slot
     L.acc = o; o = align256_hd(o + (fused ? sizeof(double) * 3 * OT_ACC_COPIES * (size_t)L.vstride : 0));
     L.trace = o; o = align256_hd(o + sizeof(unsigned long long) * 8 * OT_TRACE_SWEEPS);
     L.total = o;
@@ -1309,16 +1856,16 @@ size_t solver_ws_bytes(int M, int Ncol, bool stored) {
 }
 
 template <typename K, typename... Args>
-static int coop_launch(K kernel, int grid, cudaStream_t st, size_t smem, Args... args) {
+static int coop_launch_nt(K kernel, int grid, int nt, cudaStream_t st, size_t smem, Args... args) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return OT_ERR_CUDA;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, OT_BLOCK, smem) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, nt, smem) != cudaSuccess || nb < 1)
         return OT_ERR_UNSUPPORTED;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(OT_BLOCK);
+    cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1328,6 +1875,11 @@ static int coop_launch(K kernel, int grid, cudaStream_t st, size_t smem, Args...
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
     return e == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}
+
+template <typename K, typename... Args>
+static int coop_launch(K kernel, int grid, cudaStream_t st, size_t smem, Args... args) {
+    return coop_launch_nt(kernel, grid, OT_BLOCK, st, smem, args...);
 }
 
 template <int CPT, int R>
@@ -1365,6 +1917,32 @@ static int launch_bulk(SkArgs& A, int grid, cudaStream_t st) {
     if (cpt <= 4) return rows_max <= 8 ? launch_bulk_r<4, 8>(A, grid, st) : launch_bulk_r<4, 16>(A, grid, st);
     if (cpt <= 8) return launch_bulk_r<8, 8>(A, grid, st);
     return launch_bulk_r<16, 4>(A, grid, st);
+}
+
+// Ring kernel: NT threads, CPT columns per thread, bands of R rows, S ring stages.
+template <int NT, int CPT, int R, int S>
+static int launch_ring_t(SkArgs& A, int grid, cudaStream_t st) {
+    A.rows_max = (A.M + grid - 1) / grid;
+    const int nb_max = (A.rows_max + R - 1) / R;
+    const size_t band_bytes = (size_t)R * A.Ncol * sizeof(float);
+    const size_t state = align256_hd((size_t)(4 * NT + 2) * sizeof(double)) + (size_t)A.rows_max * 7 * sizeof(float);
+    const size_t limit = 227 * 1024 - 4096;   // the opt-in maximum less the kernel's static shared memory
+    const size_t res_bytes = align256_hd((size_t)nb_max * band_bytes);
+    A.resident = (res_bytes + state <= limit) ? 1 : 0;
+    const size_t smem = (A.resident ? res_bytes : align256_hd((size_t)S * band_bytes)) + state;
+    if (smem > limit) return OT_ERR_UNSUPPORTED;
+    return coop_launch_nt(sk_ring_kernel<NT, CPT, R, S>, grid, NT, st, smem, A);
+}
+
+static bool ring_ok(const SkArgs& A, int grid) {
+    return A.C != nullptr && A.Ncol % 4 == 0 && A.ld == A.Ncol && ((uintptr_t)A.C) % 16 == 0 && A.Ncol <= 4096 &&
+           !A.stop_l2 && (A.M + grid - 1) / grid <= 128;
+}
+
+static int launch_ring(SkArgs& A, int grid, cudaStream_t st) {
+    if (A.Ncol <= 1024) return launch_ring_t<256, 4, 8, 3>(A, grid, st);
+    if (A.Ncol <= 2048) return launch_ring_t<512, 4, 8, 3>(A, grid, st);
+    return launch_ring_t<512, 8, 4, 3>(A, grid, st);
 }
 
 size_t batch_single_ws_bytes(int m);
@@ -1411,6 +1989,10 @@ int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
         if (smem > kSmemBudget) return OT_ERR_UNSUPPORTED;
         return stored ? coop_launch(sk_twopass_kernel<false>, grid, st, smem, A)
                       : coop_launch(sk_twopass_kernel<true>, grid, st, smem, A);
+    }
+    if (ring_ok(A, grid) && !(A.debug_flags & OT_DEBUG_NO_CLUSTER) && (A.Ncol > 2048 || (A.debug_flags & OT_DEBUG_RING))) {
+        const int rc = launch_ring(A, grid, st);
+        if (rc != OT_ERR_UNSUPPORTED) return rc;
     }
     const int cpt = (A.Ncol + OT_BLOCK - 1) / OT_BLOCK;
     // the cluster kernel updates every column in every block: worth it while Ncol <= 2048

@@ -12,7 +12,6 @@ CUDA device, the call raises.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from dataclasses import dataclass
 from typing import Optional
@@ -47,6 +46,7 @@ OT_OP_UNROLLED = 3
 OT_DEBUG_WITHHOLD_ARRIVAL = 1
 OT_DEBUG_TRACE = 2
 OT_DEBUG_NO_CLUSTER = 4
+OT_DEBUG_RING = 8
 OT_STOP_L1_FULL = 0
 OT_STOP_L2_ROW = 1
 
@@ -169,7 +169,8 @@ def read_result(res: torch.Tensor) -> dict:
     return {"iters": r.iters, "status": r.status, "marg_l1": r.marg_l1, "marg_l2_col": r.marg_l2_col,
             "value": r.value, "transport_cost": r.transport_cost, "marg_l1_col": r.marg_l1_col,
             "mass": r.reserved[0],
-            "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream", 5.0: "srot", 6.0: "lot"}.get(r.reserved[1], "other")}
+            "variant": {1.0: "bulk", 2.0: "fused", 3.0: "twopass", 4.0: "stream", 5.0: "srot", 6.0: "lot",
+                        7.0: "ring"}.get(r.reserved[1], "other")}
 
 
 def ot_workspace_bytes(op: int, m_or_n: int, N: int, opt: Optional[ot_options] = None) -> int:
@@ -299,10 +300,6 @@ def cyclic_erot(a_base, b_base, eps: float, C_base=None, x=None, y=None, tol: fl
         raise OTError(res["status"], "ot_sinkhorn_reduced")
     del src
     return ReducedSolution(w=w, z=z, G=G, result=res)
-
-
-def eps_log_n(eps: float, N: int) -> float:
-    return float(eps) * math.log(N)
 
 
 def read_trace(ws: torch.Tensor) -> "np.ndarray":

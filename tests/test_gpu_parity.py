@@ -506,3 +506,66 @@ def test_paper_synthetic_erot_vs_oracle(cy, m, N):
     assert r["value"] == pytest.approx(v["value"], rel=1e-5)
     assert r["transport_cost"] == pytest.approx(v["transport_cost"], rel=1e-5)
 
+
+# ------------------------------------------------------------------ ring solver (per-thread copy ring, FP32 sweep)
+
+RING_CASES = [
+    (2100, 2, 0.05, 0, 0),      # > 2048 columns: default route, every band resident in shared memory
+    (3000, 3, 0.02, 1, 0),      # 3000 columns: the copy ring streams the bands (ragged last chunk)
+    (4096, 2, 0.01, 2, 0),      # the widest route (8 columns per thread), streaming
+    (1024, 4, 0.01, 3, 8),      # forced (OT_DEBUG_RING): 256 threads, resident
+    (1500, 2, 0.02, 4, 8),      # forced: 512 threads x 4 columns, resident
+]
+
+
+@pytest.mark.parametrize("m,N,frac,seed,flags", RING_CASES)
+def test_ring_solver_parity(cy, m, N, frac, seed, flags):
+    """The ring solver against the oracle: the same iteration count (identical stopping rule),
+    FP64 marginals of the returned potentials, potentials up to the dual constant."""
+    p = I.sector_problem(m, N, seed=seed, eps_frac=frac)
+    tol = 1e-6
+    Cb = dev(p.C_base)
+    G, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, m, N, C_base=Cb, eps=p.eps)
+    w, z, out = cy.ot_sinkhorn_reduced(m, N, dev(p.a_base), dev(p.b_base), G,
+                                       cy.options(p.eps, tol=tol, max_iter=100000, debug_flags=flags))
+    res = cy.read_result(out)
+    assert res["status"] == cy.OT_OK, res
+    assert res["variant"] == "ring"
+    assert res["marg_l1"] <= tol
+    orc = OS.cyclic_sinkhorn(p.a_base, p.b_base, p.C_base, p.eps, tol=tol)
+    assert abs(res["iters"] - orc["iters"]) <= 1, (res["iters"], orc["iters"])
+    wg, zg = host(w), host(z)
+    rl1, cl1 = fp64_row_col_errors(wg, zg, p.C_base, p.a_base, p.b_base, p.eps)
+    assert rl1 <= tol + 2e-7 and cl1 <= 1e-6, (rl1, cl1)
+    d = wg - orc["w"]
+    assert np.abs(d - d.mean()).max() <= 1e-5 * max(1.0, np.abs(orc["w"]).max()) + 10 * p.eps * 1e-6
+
+
+def test_ring_solver_warm_start_and_statuses(cy):
+    """Warm start, NOT_CONVERGED, a device-detected bad marginal and the bounded barrier on the
+    ring route (m = 2100 > 2048 columns)."""
+    p = I.sector_problem(2100, 2, seed=5, eps_frac=0.02)
+    G, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, p.m, p.N, C_base=dev(p.C_base), eps=p.eps)
+    a, b = dev(p.a_base), dev(p.b_base)
+    _, z1, o1 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps, tol=1e-3))
+    r1 = cy.read_result(o1)
+    w2, z2, o2 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps, tol=1e-6, warm_start=True), z=z1)
+    w3, z3, o3 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps, tol=1e-6))
+    r2, r3 = cy.read_result(o2), cy.read_result(o3)
+    assert r1["variant"] == r2["variant"] == r3["variant"] == "ring"
+    assert r2["status"] == r3["status"] == cy.OT_OK and r2["iters"] < r3["iters"]
+    assert abs(r1["iters"] + r2["iters"] - r3["iters"]) <= 2
+    d = host(w2) - host(w3)
+    assert np.abs(d - d.mean()).max() < 1e-4 * p.max_cost
+    _, _, o = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps, tol=1e-12, max_iter=3))
+    r = cy.read_result(o)
+    assert r["status"] == cy.OT_ERR_NOT_CONVERGED and r["iters"] == 3
+    a0 = a.clone()
+    a0[7] = 0.0
+    _, _, o = cy.ot_sinkhorn_reduced(p.m, p.N, a0, b, G, cy.options(p.eps))
+    assert cy.read_result(o)["status"] == cy.OT_ERR_ARG
+    opt = cy.options(p.eps, timeout_ns=2_000_000, debug_flags=cy.OT_DEBUG_WITHHOLD_ARRIVAL)
+    _, _, o = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, opt)
+    assert cy.read_result(o)["status"] == cy.OT_ERR_TIMEOUT
+    _, _, o = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps))
+    assert cy.read_result(o)["status"] == cy.OT_OK
