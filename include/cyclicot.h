@@ -107,18 +107,18 @@ typedef struct {
                                        [0] sweep start, [1] row phase done, [2] after the
                                        first grid barrier, [3] column phase done.
                                        bit 2 (OT_DEBUG_NO_CLUSTER): do not use the
-                                       one-barrier-per-sweep (bulk reduce-add) solver;
-                                       use the two-barrier one (comparison runs).
-                                       bit 3 (OT_DEBUG_RING): use the ring solver
-                                       (per-thread copy ring, FP32 sweep) for every
-                                       stored cost it takes (comparison runs).          */
+                                       ring or bulk-reduce solvers; use the two-barrier
+                                       FP64-partial one (comparison runs).
+                                       bit 3 (OT_DEBUG_NO_RING): do not use the ring
+                                       solvers (per-thread copy ring, FP32 sweep); use
+                                       the FP64 bulk-reduce one (comparison runs).      */
     int stop_norm;                  /* OT_STOP_L1_FULL (default) or OT_STOP_L2_ROW          */
 } ot_options;
 
 #define OT_DEBUG_WITHHOLD_ARRIVAL 1
 #define OT_DEBUG_TRACE            2
 #define OT_DEBUG_NO_CLUSTER       4
-#define OT_DEBUG_RING             8
+#define OT_DEBUG_NO_RING          8
 
 /* Device-written outcome of one solve.  64 bytes, naturally aligned. */
 typedef struct {
@@ -196,13 +196,16 @@ int ot_sinkhorn_reduced(int m, int N, const float* a_base, const float* b_base, 
  * framework that owns the device allocator, a loop that must not allocate
  * after start-up).  Arguments and results are those of ot_sinkhorn_reduced;
  * the scratch space comes from a 4 MiB array compiled into the library (one
- * per device, held until the process exits), enough for m <= 4096 on a GPU
- * with up to 152 SMs.  Returns OT_ERR_UNSUPPORTED, launching nothing, when the
- * problem needs more scratch than that.  All calls on a device share the
- * array (each call clears what must start at zero), so calls that overlap on
- * the GPU race.  The first call on a device looks up the array's address with
- * cudaGetSymbolAddress on the current device: make it before any stream
- * capture.  Nothing here allocates memory.
+ * per device, held until the process exits).  Each call checks
+ * ot_workspace_bytes(OT_OP_SINKHORN_REDUCED, m, N, opt) against the array
+ * (the need grows with m and the device's SM count; every m <= 4096 fits on a
+ * 152-SM GB300) and returns OT_ERR_UNSUPPORTED, launching nothing, when it
+ * does not fit.  All calls on a device share the array (each call clears what
+ * must start at zero), so calls that overlap on the GPU race.  The first call
+ * on a device looks up the array's address with cudaGetSymbolAddress on the
+ * current device: make it before any stream capture, and do not reset the
+ * device afterwards (the stored address would be stale).  Nothing here
+ * allocates memory.
  */
 int ot_sinkhorn_reduced_static(int m, int N, const float* a_base, const float* b_base, const float* G,
                                const ot_options* opt, double* w, double* z, ot_result* out, void* stream);

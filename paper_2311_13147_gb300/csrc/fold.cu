@@ -6,7 +6,9 @@
 // HBM-bound streaming kernel: each thread owns 4 consecutive entries (one
 // 16-byte load per block k), grid-stride over the m*m entries, grid sized to
 // a multiple of the SM count.  With points instead of stored blocks the cost
-// C_k[i][j] = |x_i - R^k y_j|^2 is formed in registers (no HBM traffic for C).
+// C_k[i][j] = |x_i - R^k y_j|^2 is formed in registers (no HBM traffic for C):
+// column strips with the N rotated targets held in registers (N <= 16), or one
+// thread per entry for larger N.
 #include "common.cuh"
 
 namespace cyc {
@@ -139,6 +141,74 @@ __global__ void __launch_bounds__(OT_BLOCK) fold_points(int m, int N, const floa
     }
 }
 
+// Points, column strips: a block takes 256 consecutive columns (one per thread) and a
+// run of rows.  Each thread rotates its target point once per item (NK registers
+// pairs), then per row forms the N costs, their minimum and, for the soft-min, the
+// sum of exp2((min - C_k) kappa) in a second pass over registers (no branch).
+// Stores are coalesced (a row of 256 consecutive entries per block).  N <= NK.
+template <int MODE, int NK>
+__global__ void __launch_bounds__(OT_BLOCK) fold_points_strip(int m, int N, const float2* __restrict__ x,
+                                                              const float2* __restrict__ y, float kappa,
+                                                              int rows_per_item, float* __restrict__ G,
+                                                              uint8_t* __restrict__ ks) {
+    __shared__ float2 rot[NK];   // (cos, sin) of 2 pi k / N
+    if (threadIdx.x < N) {
+        float s, c;
+        sincospif(2.0f * (float)threadIdx.x / (float)N, &s, &c);
+        rot[threadIdx.x] = make_float2(c, s);
+    }
+    __syncthreads();
+    const int strips = (m + OT_BLOCK - 1) / OT_BLOCK;
+    const int chunks = (m + rows_per_item - 1) / rows_per_item;
+    const long long nitems = (long long)strips * chunks;
+    const float inv = (MODE == OT_SOFTMIN) ? 1.0f / kappa : 0.f;
+    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int s = (int)(item % strips), rc = (int)(item / strips);
+        const int j = s * OT_BLOCK + threadIdx.x;
+        if (j >= m) continue;
+        const float2 yj = __ldg(y + j);
+        float yx[NK], yy[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const float2 r = rot[k < N ? k : 0];
+            yx[k] = r.x * yj.x - r.y * yj.y;
+            yy[k] = r.y * yj.x + r.x * yj.y;
+        }
+        const int i0 = rc * rows_per_item, i1 = min(m, i0 + rows_per_item);
+#pragma unroll 2
+        for (int i = i0; i < i1; ++i) {
+            const float2 xi = __ldg(x + i);
+            float c[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const float dx = xi.x - yx[k], dy = xi.y - yy[k];
+                c[k] = fmaf(dx, dx, dy * dy);
+            }
+            const long long e = (long long)i * m + j;
+            if (MODE == OT_MIN) {
+                float best = c[0];
+                int kb = 0;
+#pragma unroll
+                for (int k = 1; k < NK; ++k)
+                    if (k < N) min_step(c[k], k, best, kb);
+                G[e] = best;
+                if (ks) ks[e] = (uint8_t)kb;
+            } else {
+                float mn = c[0];
+#pragma unroll
+                for (int k = 1; k < NK; ++k)
+                    if (k < N) mn = fminf(mn, c[k]);
+                const float mk = mn * kappa;
+                float sum = 0.f;
+#pragma unroll
+                for (int k = 0; k < NK; ++k)
+                    if (k < N) sum += ex2(fmaf(-c[k], kappa, mk));
+                G[e] = fmaf(-inv, lg2(sum), mn);
+            }
+        }
+    }
+}
+
 int grid_for(long long work, int sms) {
     long long blocks = (work + OT_BLOCK - 1) / OT_BLOCK;
     long long cap = (long long)sms * 8;
@@ -182,6 +252,24 @@ extern "C" int ot_fold_cost(int mode, int m, int N, const float* C_base, const f
                 fold_blocks_scalar<OT_MIN><<<grid, OT_BLOCK, 0, st>>>(N, mm, C_base, kappa, G, kstar);
             else
                 fold_blocks_scalar<OT_SOFTMIN><<<grid, OT_BLOCK, 0, st>>>(N, mm, C_base, kappa, G, kstar);
+        }
+    } else if (N <= 16) {
+        // column strips x runs of rows: about 4 items per SM
+        const int strips = (m + OT_BLOCK - 1) / OT_BLOCK;
+        int rpi = (int)(((long long)m * strips + 4LL * sms - 1) / (4LL * sms));
+        if (rpi < 16) rpi = 16;
+        const long long items = (long long)strips * ((m + rpi - 1) / rpi);
+        const int grid = (int)(items < 4LL * sms ? items : 4LL * sms);
+        auto launch = [&](auto kern) { kern<<<grid, OT_BLOCK, 0, st>>>(m, N, (const float2*)x, (const float2*)y, kappa,
+                                                                      rpi, G, kstar); };
+        if (mode == OT_MIN) {
+            if (N <= 4) launch(fold_points_strip<OT_MIN, 4>);
+            else if (N <= 8) launch(fold_points_strip<OT_MIN, 8>);
+            else launch(fold_points_strip<OT_MIN, 16>);
+        } else {
+            if (N <= 4) launch(fold_points_strip<OT_SOFTMIN, 4>);
+            else if (N <= 8) launch(fold_points_strip<OT_SOFTMIN, 8>);
+            else launch(fold_points_strip<OT_SOFTMIN, 16>);
         }
     } else {
         const int grid = grid_for(mm, sms);

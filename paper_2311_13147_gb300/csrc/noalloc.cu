@@ -10,10 +10,11 @@
 // array compiled into this library.
 //
 // Limits and sharing:
-// - The array holds kStaticScratchBytes (4 MiB).  That covers block sizes
-//   m <= 4096 on a GPU with up to 152 SMs (the workspace grows with m and
-//   with the SM count); larger requests are rejected with OT_ERR_UNSUPPORTED
-//   before anything is launched.
+// - The array holds kStaticScratchBytes (4 MiB).  Each call compares that with
+//   ot_workspace_bytes for its (m, N, options), which grows with m and with the
+//   device's SM count; requests that do not fit are rejected with
+//   OT_ERR_UNSUPPORTED before anything is launched.  On a 152-SM GB300 every
+//   m <= 4096 fits.
 // - Every GPU that loads the library holds its own copy of the array until
 //   the process exits.
 // - All calls on a device share that one array and it keeps the contents of
@@ -23,7 +24,9 @@
 //   example on two streams at once) race on the array and give wrong results.
 // - The first call on a device looks up the array's device address with
 //   cudaGetSymbolAddress (that device must be current); make that first call
-//   before any stream capture begins.
+//   before any stream capture begins.  The address is kept for the rest of the
+//   process, so resetting the device (cudaDeviceReset) after that first call is
+//   not supported: the module is loaded again and the array may move.
 // - Neither this entry point nor anything it calls allocates memory.
 #include <mutex>
 

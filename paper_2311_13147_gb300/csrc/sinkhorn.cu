@@ -1541,6 +1541,533 @@ __global__ void __launch_bounds__(NT, 1) sk_ring_kernel(SkArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Ping-pong ring kernel: two independent warp groups, owner-reduced columns
+// ---------------------------------------------------------------------------
+//
+// The ring kernel's sweep with the block split into two groups of 256 threads
+// that take alternate bands of the block's rows.  Each group synchronises on
+// its own named barrier only, so one group's row reduction overlaps the other
+// group's exponentials.  Both groups hold every column of the block
+// (thread t of a group owns columns 4 (t + 256 q) + v), and their column
+// partials are added in shared memory at the end of the row phase.
+//
+// Column exchange (no FP64 and no atomics: deterministic): every block stores
+// its FP32 column partials and row-error term; grid barrier; block B reduces
+// the ~m/G columns it owns over all blocks' partials (compensated FP32, fixed
+// order), updates their potentials and publishes them as (hi, lo) pairs;
+// grid barrier; every thread reads the potentials of its columns.  The row-
+// error terms are summed in the same fixed order in every block, so every
+// block takes the same stopping decision.
+
+#define PP_G 256   // threads per group
+
+typedef unsigned long long pf2;   // two packed FP32 values (f32x2 instructions)
+__device__ __forceinline__ pf2 p2(float a, float b) {
+    pf2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 u2(pf2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ pf2 fma_p2(pf2 a, pf2 b, pf2 c) {
+    pf2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ pf2 add_p2(pf2 a, pf2 b) {
+    pf2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ pf2 ex2_p2(pf2 x) {
+    const float2 v = u2(x);
+    return p2(ex2(v.x), ex2(v.y));
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(PP_G) : "memory");
+}
+
+// Sum of R per-lane values over a warp for all R at once (R = 2: one transposing
+// step, then plain xor steps).  Lane l ends with the total of value (l >> 4) & 1.
+template <int R>
+__device__ __forceinline__ float warp_reduce_rows2(float (&v)[R], int lane) {
+    if constexpr (R == 2) {
+        const bool up = (lane & 16) != 0;
+        const float keep = up ? v[1] : v[0];
+        const float send = up ? v[0] : v[1];
+        float x = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+    } else {
+        return warp_reduce_rows<R, false>(v, lane);
+    }
+}
+
+// Copies of band `band` into stage `st` of group g (this thread's slots only).
+template <int CPT, int R>
+__device__ __forceinline__ void pp_issue(const SkArgs& A, float* gring, int st, int r_beg, int r_end, int band,
+                                         int gt, unsigned cvalid) {
+    const int rb = r_beg + band * R;
+    const int nr = min(R, r_end - rb);
+    float* dst = gring + (size_t)st * R * A.Ncol + 4 * gt;
+    const float* src = A.C + (long long)rb * A.ld + 4 * gt;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r < nr) {
+#pragma unroll
+            for (int q = 0; q < CPT / 4; ++q)
+                if (cvalid & (1u << q)) cp_async16(dst + (size_t)r * A.Ncol + 4 * PP_G * q, src + (long long)r * A.ld + 4 * PP_G * q);
+        }
+    }
+}
+
+// One band of up to R rows for group g.  SAFE: explicit max shift (first sweep, and
+// the rare redo when a row sum left the safe range); GSRC: costs from global memory.
+// Returns true when some row sum left the safe range (uniform over the group).
+template <int CPT, int R, bool SAFE, bool GSRC, typename Refill>
+__device__ __forceinline__ bool pp_band(const SkArgs& A, const RingRows& RS, const float* sb, long long rstride,
+                                        int rb, int lb, int nr, int cur, int nxt, int g, int gt, unsigned cvalid,
+                                        const pf2 (&gh)[CPT / 2], const pf2 (&cf)[CPT / 2], pf2 (&e)[R][CPT / 2],
+                                        float (&u)[R], float& l1, float (*s_red)[8], Refill refill) {
+    constexpr int NV = CPT / 4;
+    const int lane = gt & 31, wg = gt >> 5;
+    const int rm = A.rows_max;
+    const pf2 nk = p2(-A.kappa, -A.kappa);
+    constexpr int LOGR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
+    const int my_row = (lane >> (5 - LOGR)) & (R - 1);
+    const bool writer = (lane & ((32 >> LOGR) - 1)) == 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool rv = r < nr;
+        const float F = (SAFE || !rv) ? 0.f : RS.hi[cur * rm + lb + r];
+        const pf2 FF = p2(F, F);
+        const float* srow = sb + (rv ? r : 0) * rstride + 4 * gt;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            if (rv && (cvalid & (1u << q))) {
+                const float4 c = GSRC ? __ldg(reinterpret_cast<const float4*>(srow + 4 * PP_G * q))
+                                      : *reinterpret_cast<const float4*>(srow + 4 * PP_G * q);
+                e[r][2 * q] = add_p2(fma_p2(p2(c.x, c.y), nk, gh[2 * q]), FF);
+                e[r][2 * q + 1] = add_p2(fma_p2(p2(c.z, c.w), nk, gh[2 * q + 1]), FF);
+            } else {
+                e[r][2 * q] = e[r][2 * q + 1] = p2(-INFINITY, -INFINITY);
+            }
+        }
+    }
+    refill();   // the stage's costs are in registers
+    float Fsafe = 0.f;
+    if (SAFE) {
+        float mx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float m = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < CPT / 2; ++q) {
+                const float2 v = u2(e[r][q]);
+                m = fmaxf(m, fmaxf(v.x, v.y));
+            }
+            mx[r] = m;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) mx[r] = warp_max(mx[r]);
+        if (lane == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) s_red[r][wg] = mx[r];
+        }
+        group_sync(g);
+        float mm = -INFINITY;
+        if (lane < nr) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) mm = fmaxf(mm, s_red[lane][w]);
+        }
+        Fsafe = (mm > -INFINITY) ? -mm : 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float F = __shfl_sync(0xffffffffu, Fsafe, r);
+            const pf2 FF = p2(F, F);
+#pragma unroll
+            for (int q = 0; q < CPT / 2; ++q) e[r][q] = add_p2(e[r][q], FF);
+        }
+        group_sync(g);   // s_red is reused for the sums below
+    }
+    float ps[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        pf2 s2 = p2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < CPT / 2; ++q) {
+            e[r][q] = ex2_p2(e[r][q]);
+            s2 = fma_p2(e[r][q], cf[q], s2);
+        }
+        const float2 s = u2(s2);
+        ps[r] = s.x + s.y;
+    }
+    const float wsum = warp_reduce_rows2<R>(ps, lane);
+    if (writer) s_red[my_row][wg] = wsum;
+    group_sync(g);
+    float S = 1.f, alpha = 0.f;
+    if (lane < nr) {
+        const float4* rr = reinterpret_cast<const float4*>(s_red[lane]);
+        const float4 p0 = rr[0], p1 = rr[1];
+        S = ((p0.x + p0.y) + (p0.z + p0.w)) + ((p1.x + p1.y) + (p1.z + p1.w));
+        alpha = RS.alpha[lb + lane];
+    }
+    const bool ok = (lane >= nr) || sum_ok(S);
+    const float ul = (lane < nr) ? __fdividef(alpha, S) : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = __shfl_sync(0xffffffffu, ul, r);
+    const bool bad = !__all_sync(0xffffffffu, ok);
+    if (wg == 0 && lane < nr) {
+        const int li = lb + lane;
+        const float d = lg2(__fdividef(S, alpha));
+        float base;
+        if (!SAFE) {
+            l1 += ok ? fabsf(fmaf(S, RS.fr[cur * rm + li] - 1.0f, S - alpha)) : 1e30f;
+            base = RS.hi[cur * rm + li];
+        } else {
+            base = Fsafe;
+        }
+        if (ok) {
+            float h, l;
+            two_diff(base, d, h, l);
+            const float f = ex2(l);
+            RS.hi[nxt * rm + li] = h;
+            RS.lo[nxt * rm + li] = l;
+            RS.fr[nxt * rm + li] = f;
+            A.fhi[nxt * A.M + rb + lane] = h;
+            A.frf[nxt * A.M + rb + lane] = f;
+        }
+    }
+    return bad;
+}
+
+template <int CPT, int R, int S>
+__global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
+    constexpr int NV = CPT / 4;
+    constexpr int NT = 2 * PP_G;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(16) float s_red[2][2][R][8];   // [group][band parity][row][warp of the group]
+    __shared__ float s_redf[NW];
+    __shared__ float s_own[16][2][33];                  // owner phase: [slice][sum, comp][column]
+    __shared__ float s_l1g[2];
+    __shared__ float s_L1;
+    __shared__ int s_fix;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int g = tid / PP_G, gt = tid % PP_G;
+    const int B = blockIdx.x, G = gridDim.x;
+    const int Nc = A.Ncol;
+    const int r_beg = (int)((long long)A.M * B / G), r_end = (int)((long long)A.M * (B + 1) / G);
+    const int o_beg = (int)((long long)Nc * B / G), o_end = (int)((long long)Nc * (B + 1) / G);
+    const int nown = o_end - o_beg;   // <= 32 (checked by the launcher)
+    const int nbands = (r_end - r_beg + R - 1) / R;
+    const int gbands = (nbands - g + 1) / 2;          // bands g, g + 2, ... of this block
+    const bool resident = A.resident != 0;
+    const int nstage = resident ? (nbands + 1) / 2 : S;
+    unsigned cvalid = 0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) cvalid |= (4 * (gt + PP_G * q) < Nc) ? (1u << q) : 0u;
+
+    // dynamic shared memory: [group 0 ring][group 1 ring][group-1 column partials][row state][owned columns]
+    const size_t gring_floats = (size_t)nstage * R * Nc;
+    float* gring = reinterpret_cast<float*>(dsm) + (size_t)g * gring_floats;
+    unsigned char* p = dsm + align256_hd(2 * gring_floats * sizeof(float));
+    float* s_acc = reinterpret_cast<float*>(p);                 // [PP_G][CPT]
+    p += align256_hd((size_t)PP_G * CPT * sizeof(float));
+    RingRows RS;
+    RS.hi = reinterpret_cast<float*>(p);
+    RS.lo = RS.hi + 2 * A.rows_max;
+    RS.fr = RS.lo + 2 * A.rows_max;
+    RS.alpha = RS.fr + 2 * A.rows_max;
+    p += align256_hd((size_t)A.rows_max * 7 * sizeof(float));
+    float* s_ohi = reinterpret_cast<float*>(p);   // owned columns: potential (hi, lo), 2^lo, beta
+    float* s_olo = s_ohi + 32;
+    float* s_ocf = s_olo + 32;
+    float* s_obt = s_ocf + 32;
+    float2* gam2 = reinterpret_cast<float2*>(A.gc);   // [2][Ncol] published (hi, lo) per state
+    unsigned epoch = 0;
+
+    // ---- first copies of this group's bands
+    long long issued = 0, consumed = 0;
+    if (gbands > 0) {
+        if (resident) {
+            for (int bb = 0; bb < gbands; ++bb) pp_issue<CPT, R>(A, gring, bb, r_beg, r_end, 2 * bb + g, gt, cvalid);
+            cp_async_commit();
+        } else {
+            for (int s = 0; s < S; ++s) {
+                pp_issue<CPT, R>(A, gring, s, r_beg, r_end, 2 * (s % gbands) + g, gt, cvalid);
+                cp_async_commit();
+            }
+            issued = S;
+        }
+    }
+
+    __shared__ double s_dred[NW];
+    double sa = 0.0, sb = 0.0;
+    int badm = 0;
+    for (int i = tid; i < A.M; i += NT) { const float v = A.a[i]; badm |= !(v > 0.f && v < INFINITY); sa += v; }
+    for (int j = tid; j < Nc; j += NT) { const float v = A.b[j]; badm |= !(v > 0.f && v < INFINITY); sb += v; }
+    sa = warp_sum(sa);
+    sb = warp_sum(sb);
+    if (lane == 0) s_dred[wid] = sa;
+    __syncthreads();
+    double tsa = 0.0;
+    for (int w = 0; w < NW; ++w) tsa += s_dred[w];
+    __syncthreads();
+    if (lane == 0) s_dred[wid] = sb;
+    __syncthreads();
+    double tsb = 0.0;
+    for (int w = 0; w < NW; ++w) tsb += s_dred[w];
+    const bool args_ok = __syncthreads_or(badm) == 0;
+    const double inv_sa = 1.0 / tsa, inv_sb = 1.0 / tsb;
+    for (int li = tid; li < r_end - r_beg; li += NT) RS.alpha[li] = (float)((double)A.a[r_beg + li] * inv_sa);
+    // potentials of this thread's columns, and the owned columns' full state
+    pf2 gh[CPT / 2], cf[CPT / 2];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        float hv[4], cv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = 4 * (gt + PP_G * q) + v;
+            float hi = 0.f, lo = 0.f;
+            if (j < Nc && A.warm) split_f64(A.g_out[j] / A.unit, hi, lo);
+            hv[v] = hi;
+            cv[v] = (j < Nc) ? ex2(lo) : 0.f;
+        }
+        gh[2 * q] = p2(hv[0], hv[1]);
+        gh[2 * q + 1] = p2(hv[2], hv[3]);
+        cf[2 * q] = p2(cv[0], cv[1]);
+        cf[2 * q + 1] = p2(cv[2], cv[3]);
+    }
+    if (tid < nown) {
+        const int j = o_beg + tid;
+        float hi = 0.f, lo = 0.f;
+        if (A.warm) split_f64(A.g_out[j] / A.unit, hi, lo);
+        s_ohi[tid] = hi;
+        s_olo[tid] = lo;
+        s_ocf[tid] = ex2(lo);
+        s_obt[tid] = (float)((double)A.b[j] * inv_sb);
+    }
+    if (tid == 0) s_fix = 0;
+    const float tolf = (float)A.tol;
+    bool go = args_ok;
+    if (go && (A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && B == 0) {
+        withhold_arrival(A.ctrl, A.timeout_ns);
+        go = false;
+    } else if (go) {
+        go = grid_sync(A.ctrl, G, A.timeout_ns, epoch);
+    }
+
+    for (int t = 1; go; ++t) {
+        const int cur = (t - 1) & 1, nxt = cur ^ 1;
+        trace_mark(A, t, 0);
+        pf2 acc[CPT / 2];
+#pragma unroll
+        for (int q = 0; q < CPT / 2; ++q) acc[q] = p2(0.f, 0.f);
+        float l1 = 0.f;
+        pf2 e[R][CPT / 2];
+        if (resident && t == 1) cp_async_wait_all();
+        for (int bb = 0; bb < gbands; ++bb) {
+            const int b = 2 * bb + g;
+            const int rb = r_beg + b * R;
+            const int lb = b * R;
+            const int nr = min(R, r_end - rb);
+            int st = bb;
+            if (!resident) {
+                cp_async_wait<S - 1>();
+                st = (int)(consumed % S);
+            }
+            const float* sbase = gring + (size_t)st * R * Nc;
+            auto refill = [&]() {
+                if (!resident) {
+                    pp_issue<CPT, R>(A, gring, st, r_beg, r_end, 2 * (int)(issued % gbands) + g, gt, cvalid);
+                    cp_async_commit();
+                }
+            };
+            auto none = []() {};
+            float u[R];
+            bool bad;
+            if (t == 1)
+                bad = pp_band<CPT, R, true, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf, e, u,
+                                                   l1, s_red[g][bb & 1], refill);
+            else
+                bad = pp_band<CPT, R, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf, e,
+                                                    u, l1, s_red[g][bb & 1], refill);
+            if (!resident) { ++consumed; ++issued; }
+            if (bad) {   // uniform over the group: redo the band max-shifted from the costs in global memory
+                group_sync(g);
+                float dummy = 0.f;
+                if (pp_band<CPT, R, true, true>(A, RS, A.C + (long long)rb * A.ld, A.ld, rb, lb, nr, cur, nxt, g, gt,
+                                                cvalid, gh, cf, e, u, dummy, s_red[g][bb & 1], none))
+                    if (gt == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
+                group_sync(g);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < nr) {
+                    const pf2 uu = p2(u[r], u[r]);
+#pragma unroll
+                    for (int q = 0; q < CPT / 2; ++q) acc[q] = fma_p2(uu, e[r][q], acc[q]);
+                }
+            }
+        }
+        trace_mark(A, t, 4);
+        // ---- the two groups' column partials and row-error terms -> one per block, to global memory
+        if (wid == 0 || wid == PP_G / 32) {
+            const float v = warp_sum(l1);
+            if (lane == 0) s_l1g[g] = v;
+        }
+        if (g == 1) {
+#pragma unroll
+            for (int q = 0; q < CPT / 2; ++q) reinterpret_cast<pf2*>(s_acc)[q * PP_G + gt] = acc[q];
+        }
+        __syncthreads();
+        if (g == 0) {
+            float* prow = A.part + (long long)B * A.pstride;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                if (cvalid & (1u << q)) {
+                    const float2 a0 = u2(add_p2(acc[2 * q], reinterpret_cast<const pf2*>(s_acc)[(2 * q) * PP_G + gt]));
+                    const float2 a1 =
+                        u2(add_p2(acc[2 * q + 1], reinterpret_cast<const pf2*>(s_acc)[(2 * q + 1) * PP_G + gt]));
+                    __stcg(reinterpret_cast<float4*>(prow + 4 * (gt + PP_G * q)), make_float4(a0.x, a0.y, a1.x, a1.y));
+                }
+            }
+            if (gt == 0) reinterpret_cast<float*>(A.l1part)[B] = s_l1g[0] + s_l1g[1];
+        }
+        trace_mark(A, t, 1);
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
+        trace_mark(A, t, 2);
+
+        // ---- owner phase: the row L1 of the state after t - 1 iterations (same order in every block),
+        // then the owned columns' sums over all blocks (compensated FP32, fixed order)
+        if (wid == 0) {
+            float s = 0.f, c = 0.f;
+            for (int b2 = lane; b2 < G; b2 += 32) kahan_add(s, c, __ldcg(reinterpret_cast<const float*>(A.l1part) + b2));
+            s -= c;
+            s = warp_sum(s);
+            if (lane == 0) s_L1 = s;
+        }
+        {
+            const int c = tid & 31, sl = tid >> 5;   // column of the owned range, slice of the blocks
+            float s = 0.f, cp = 0.f;
+            if (c < nown) {
+                float v[10];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) {
+                    const int b2 = sl + 16 * k;
+                    v[k] = (b2 < G) ? __ldcg(A.part + (long long)b2 * A.pstride + o_beg + c) : 0.f;
+                }
+                for (int k = 0; k < 10; ++k) kahan_add(s, cp, v[k]);
+                for (int b2 = sl + 160; b2 < G; b2 += 16) kahan_add(s, cp, __ldcg(A.part + (long long)b2 * A.pstride + o_beg + c));
+            }
+            s_own[sl][0][c] = s;
+            s_own[sl][1][c] = cp;
+        }
+        __syncthreads();
+        const float L1 = s_L1;
+        trace_mark(A, t, 5);
+        int stt = -1;
+        if (t - 1 >= 1) {
+            if (L1 != L1) stt = OT_ERR_NONFINITE;
+            else if ((t - 1) % A.check_every == 0 && L1 <= tolf) stt = OT_OK;
+            else if (t - 1 >= A.max_iter) stt = OT_ERR_NOT_CONVERGED;
+        }
+        if (stt >= 0) {
+            for (int li = tid; li < r_end - r_beg; li += NT)
+                A.f_out[r_beg + li] =
+                    ((double)RS.hi[cur * A.rows_max + li] + (double)RS.lo[cur * A.rows_max + li]) * A.unit + A.f_shift;
+            if (tid < nown) A.g_out[o_beg + tid] = ((double)s_ohi[tid] + (double)s_olo[tid]) * A.unit;
+            if (B == 0 && tid == 0) {
+                A.res->iters = t - 1;
+                A.res->status = stt;
+                A.res->marg_l1 = (double)L1;
+                A.res->marg_l2_col = -1.0;
+                A.res->value = 0.0;
+                A.res->transport_cost = 0.0;
+                A.res->marg_l1_col = -1.0;
+                A.res->reserved[0] = 0.0;
+                A.res->reserved[1] = OT_VARIANT_RING;
+            }
+            break;
+        }
+        if (wid == 0 && lane < nown) {
+            float s = 0.f, cp = 0.f;
+#pragma unroll
+            for (int sl = 0; sl < 16; ++sl) {
+                kahan_add(s, cp, s_own[sl][0][lane]);
+                kahan_add(s, cp, -s_own[sl][1][lane]);
+            }
+            s -= cp;
+            const float Rj = s * s_ocf[lane];   // column sum of the plan after the row update
+            if (Rj != Rj) {
+                set_status(A.ctrl, OT_ERR_NONFINITE);
+            } else if (Rj > 1e-30f && Rj < 1e30f) {
+                float hi = s_ohi[lane], lo = s_olo[lane];
+                df_sub(hi, lo, lg2(__fdividef(Rj, s_obt[lane])));
+                s_ohi[lane] = hi;
+                s_olo[lane] = lo;
+                s_ocf[lane] = ex2(lo);
+                gam2[nxt * Nc + o_beg + lane] = make_float2(hi, lo);
+            } else {
+                atomicAdd(&s_fix, 1);
+                s_ohi[lane] = NAN;   // marks the column for the fallback below
+            }
+        }
+        __syncthreads();
+        if (s_fix > 0) {   // rare: a column sum out of range, recomputed with an explicit max over the column
+            for (int c = 0; c < nown; ++c) {
+                if (!(s_ohi[c] == s_ohi[c])) {
+                    float h, l;
+                    ring_column_fallback<NT>(A, o_beg + c, nxt, s_obt[c], s_redf, h, l);
+                    if (tid == 0) {
+                        s_ohi[c] = h;
+                        s_olo[c] = l;
+                        s_ocf[c] = ex2(l);
+                        gam2[nxt * Nc + o_beg + c] = make_float2(h, l);
+                    }
+                    __syncthreads();
+                }
+            }
+            if (tid == 0) s_fix = 0;
+        }
+        trace_mark(A, t, 6);
+        if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
+        // ---- every thread: the new potentials of its columns
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            if (cvalid & (1u << q)) {
+                const float4* src = reinterpret_cast<const float4*>(gam2 + nxt * Nc + 4 * (gt + PP_G * q));
+                const float4 h01 = __ldcg(src), h23 = __ldcg(src + 1);   // (hi, lo) of 4 columns
+                gh[2 * q] = p2(h01.x, h01.z);
+                gh[2 * q + 1] = p2(h23.x, h23.z);
+                cf[2 * q] = p2(ex2(h01.y), ex2(h01.w));
+                cf[2 * q + 1] = p2(ex2(h23.y), ex2(h23.w));
+            }
+        }
+        trace_mark(A, t, 3);
+    }
+    if (!args_ok) {
+        if (B == 0 && tid == 0) {
+            A.res->iters = 0;
+            A.res->status = OT_ERR_ARG;
+            A.res->marg_l1 = -1.0;
+            A.res->reserved[1] = OT_VARIANT_RING;
+        }
+    } else if (!go) {
+        fail_exit(A);
+    }
+    cp_async_wait_all();   // no copy may still target this block's shared memory when it exits
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Two-pass kernel (any width; stored or on-the-fly cost)
 // ---------------------------------------------------------------------------
 
@@ -1810,7 +2337,7 @@ static WsLayout ws_layout(int M, int Ncol, int grid, bool fused) {
     L.fhi = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)M);
     L.frf = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)M);
     L.gam = o; o = align256_hd(o + sizeof(double) * 2 * (size_t)Ncol);
-    L.gc = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)Ncol);
+    L.gc = o; o = align256_hd(o + sizeof(float) * 4 * (size_t)Ncol);   // also [2][Ncol] (hi, lo) pairs
     L.cf = o; o = align256_hd(o + sizeof(float) * 2 * (size_t)Ncol);
     L.part = o; o = align256_hd(o + (fused ? sizeof(float) * (size_t)grid * L.pstride : 0));
     L.l1part = o; o = align256_hd(o + sizeof(double) * (size_t)grid);
@@ -1939,10 +2466,28 @@ static bool ring_ok(const SkArgs& A, int grid) {
            !A.stop_l2 && (A.M + grid - 1) / grid <= 128;
 }
 
+template <int CPT, int R, int S>
+static int launch_pp_t(SkArgs& A, int grid, cudaStream_t st) {
+    A.rows_max = (A.M + grid - 1) / grid;
+    if ((A.Ncol + grid - 1) / grid > 32) return OT_ERR_UNSUPPORTED;   // owned columns per block
+    const int nb_max = (A.rows_max + R - 1) / R;
+    const size_t band_bytes = (size_t)R * A.Ncol * sizeof(float);
+    const size_t state = align256_hd((size_t)PP_G * CPT * sizeof(float)) +
+                         align256_hd((size_t)A.rows_max * 7 * sizeof(float)) + 4 * 32 * sizeof(float);
+    const size_t limit = 227 * 1024 - 8192;   // the opt-in maximum less the kernel's static shared memory
+    const size_t res_bytes = align256_hd(2 * (size_t)((nb_max + 1) / 2) * band_bytes);
+    A.resident = (res_bytes + state <= limit) ? 1 : 0;
+    const size_t smem = (A.resident ? res_bytes : align256_hd(2 * (size_t)S * band_bytes)) + state;
+    if (smem > limit) return OT_ERR_UNSUPPORTED;
+    return coop_launch_nt(sk_pp_kernel<CPT, R, S>, grid, 2 * PP_G, st, smem, A);
+}
+
+// Up to 1024 columns the single-group ring kernel (one barrier per sweep, bulk FP64 adds at L2)
+// is faster: the column exchange dominates small sweeps.  Wider costs take the ping-pong kernel.
 static int launch_ring(SkArgs& A, int grid, cudaStream_t st) {
     if (A.Ncol <= 1024) return launch_ring_t<256, 4, 8, 3>(A, grid, st);
-    if (A.Ncol <= 2048) return launch_ring_t<512, 4, 8, 3>(A, grid, st);
-    return launch_ring_t<512, 8, 4, 3>(A, grid, st);
+    if (A.Ncol <= 2048) return launch_pp_t<8, 4, 3>(A, grid, st);
+    return launch_pp_t<16, 2, 3>(A, grid, st);
 }
 
 size_t batch_single_ws_bytes(int m);
@@ -1990,7 +2535,7 @@ int run_solver(SkArgs A, void* ws, size_t ws_bytes, cudaStream_t st) {
         return stored ? coop_launch(sk_twopass_kernel<false>, grid, st, smem, A)
                       : coop_launch(sk_twopass_kernel<true>, grid, st, smem, A);
     }
-    if (ring_ok(A, grid) && !(A.debug_flags & OT_DEBUG_NO_CLUSTER) && (A.Ncol > 2048 || (A.debug_flags & OT_DEBUG_RING))) {
+    if (ring_ok(A, grid) && !(A.debug_flags & (OT_DEBUG_NO_CLUSTER | OT_DEBUG_NO_RING))) {
         const int rc = launch_ring(A, grid, st);
         if (rc != OT_ERR_UNSUPPORTED) return rc;
     }

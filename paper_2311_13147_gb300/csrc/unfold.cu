@@ -100,34 +100,31 @@ __global__ void __launch_bounds__(OT_BLOCK) unfold_kernel(int m, int N, const fl
 }
 
 // EROT unfold, 4 consecutive columns per thread (m % 4 == 0, 16-byte aligned
-// buffers): tiles of UT_R rows x 1024 columns, the tile's cost rows (or
-// points) loaded before any exponential, stores with the streaming hint.
+// buffers).  An item is one block k, a strip of 1024 columns and a run of rows:
+// the strip's column potentials are split into (hi, lo) once per item (the FP64
+// work of this GPU is slow), then sub-tiles of UT_R rows are formed with the
+// tile's cost rows (or points) loaded before any exponential, stores with the
+// streaming hint.
 #define UT_C4 (4 * OT_BLOCK)
 template <bool POINTS>
 __global__ void __launch_bounds__(OT_BLOCK) unfold_erot_vec4(int m, int N, const double* __restrict__ w,
                                                              const double* __restrict__ z,
                                                              const float* __restrict__ C, const float2* __restrict__ x,
                                                              const float2* __restrict__ y, float kappa, int dense,
-                                                             float* __restrict__ T) {
+                                                             int rows_per_item, float* __restrict__ T) {
     __shared__ float s_wh[UT_R], s_wl[UT_R];
     __shared__ float4 s_zh[OT_BLOCK], s_zl[OT_BLOCK];
     __shared__ float2 s_rot;
-    const int tiles_r = (m + UT_R - 1) / UT_R, tiles_c = (m + UT_C4 - 1) / UT_C4;
-    const long long ntiles = (long long)N * tiles_r * tiles_c;
+    const int strips = (m + UT_C4 - 1) / UT_C4, chunks = (m + rows_per_item - 1) / rows_per_item;
+    const long long nitems = (long long)N * strips * chunks;
     const long long n = (long long)N * m;
     const int m4 = m >> 2;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int k = (int)(tile / ((long long)tiles_r * tiles_c));
-        const int rem = (int)(tile - (long long)k * tiles_r * tiles_c);
-        const int i0 = (rem / tiles_c) * UT_R, g0 = (rem % tiles_c) * OT_BLOCK;   // float4 column index
+    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = (int)(item / ((long long)strips * chunks));
+        const int rem = (int)(item - (long long)k * strips * chunks);
+        const int r_beg = (rem / strips) * rows_per_item, g0 = (rem % strips) * OT_BLOCK;   // float4 column index
+        const int r_end = min(m, r_beg + rows_per_item);
         __syncthreads();
-        if (threadIdx.x < UT_R) {
-            const int i = i0 + threadIdx.x;
-            float hi = 0.f, lo = 0.f;
-            if (i < m) split_f64(w[i] * (double)kappa, hi, lo);
-            s_wh[threadIdx.x] = hi;
-            s_wl[threadIdx.x] = lo;
-        }
         {
             const int g = g0 + threadIdx.x;
             float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
@@ -145,52 +142,64 @@ __global__ void __launch_bounds__(OT_BLOCK) unfold_erot_vec4(int m, int N, const
         }
         __syncthreads();
         const int g = g0 + threadIdx.x;
-        if (g >= m4) continue;
+        const bool gv = g < m4;
         const float4 zh = s_zh[threadIdx.x], zl = s_zl[threadIdx.x];
         float2 yk[4];
         if (POINTS) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float2 yj = y[4 * g + c];
+                const float2 yj = gv ? y[4 * g + c] : make_float2(0.f, 0.f);
                 yk[c] = make_float2(s_rot.x * yj.x - s_rot.y * yj.y, s_rot.y * yj.x + s_rot.x * yj.y);
             }
         }
-        const int nr = min(UT_R, m - i0);
-        float4 cst[UT_R];
+        for (int i0 = r_beg; i0 < r_end; i0 += UT_R) {
+            __syncthreads();   // the previous sub-tile's row potentials are no longer read
+            if (threadIdx.x < UT_R) {
+                const int i = i0 + threadIdx.x;
+                float hi = 0.f, lo = 0.f;
+                if (i < r_end) split_f64(w[i] * (double)kappa, hi, lo);
+                s_wh[threadIdx.x] = hi;
+                s_wl[threadIdx.x] = lo;
+            }
+            __syncthreads();
+            if (!gv) continue;
+            const int nr = min(UT_R, r_end - i0);
+            float4 cst[UT_R];
 #pragma unroll
-        for (int r = 0; r < UT_R; ++r) {
-            if (r < nr) {
-                const int i = i0 + r;
-                if (POINTS) {
-                    const float2 xi = x[i];
-                    float cc[4];
+            for (int r = 0; r < UT_R; ++r) {
+                if (r < nr) {
+                    const int i = i0 + r;
+                    if (POINTS) {
+                        const float2 xi = x[i];
+                        float cc[4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float dx = xi.x - yk[c].x, dy = xi.y - yk[c].y;
-                        cc[c] = fmaf(dx, dx, dy * dy);
+                        for (int c = 0; c < 4; ++c) {
+                            const float dx = xi.x - yk[c].x, dy = xi.y - yk[c].y;
+                            cc[c] = fmaf(dx, dx, dy * dy);
+                        }
+                        cst[r] = make_float4(cc[0], cc[1], cc[2], cc[3]);
+                    } else {
+                        cst[r] = __ldg(reinterpret_cast<const float4*>(C + (long long)k * m * m + (long long)i * m) + g);
                     }
-                    cst[r] = make_float4(cc[0], cc[1], cc[2], cc[3]);
-                } else {
-                    cst[r] = __ldg(reinterpret_cast<const float4*>(C + (long long)k * m * m + (long long)i * m) + g);
                 }
             }
-        }
 #pragma unroll
-        for (int r = 0; r < UT_R; ++r) {
-            if (r < nr) {
-                const int i = i0 + r;
-                const float wh = s_wh[r], wl = s_wl[r];
-                float4 v;
-                v.x = ex2(fmaf(cst[r].x, -kappa, wh + zh.x) + (wl + zl.x));
-                v.y = ex2(fmaf(cst[r].y, -kappa, wh + zh.y) + (wl + zl.y));
-                v.z = ex2(fmaf(cst[r].z, -kappa, wh + zh.z) + (wl + zl.z));
-                v.w = ex2(fmaf(cst[r].w, -kappa, wh + zh.w) + (wl + zl.w));
-                if (!dense) {
-                    __stcs(reinterpret_cast<float4*>(T + (long long)k * m * m + (long long)i * m) + g, v);
-                } else {
-                    for (int rb = 0; rb < N; ++rb) {
-                        const int cb = (rb + k) % N;
-                        __stcs(reinterpret_cast<float4*>(T + ((long long)rb * m + i) * n + (long long)cb * m) + g, v);
+            for (int r = 0; r < UT_R; ++r) {
+                if (r < nr) {
+                    const int i = i0 + r;
+                    const float wh = s_wh[r], wl = s_wl[r];
+                    float4 v;
+                    v.x = ex2(fmaf(cst[r].x, -kappa, wh + zh.x) + (wl + zl.x));
+                    v.y = ex2(fmaf(cst[r].y, -kappa, wh + zh.y) + (wl + zl.y));
+                    v.z = ex2(fmaf(cst[r].z, -kappa, wh + zh.z) + (wl + zl.z));
+                    v.w = ex2(fmaf(cst[r].w, -kappa, wh + zh.w) + (wl + zl.w));
+                    if (!dense) {
+                        __stcs(reinterpret_cast<float4*>(T + (long long)k * m * m + (long long)i * m) + g, v);
+                    } else {
+                        for (int rb = 0; rb < N; ++rb) {
+                            const int cb = (rb + k) % N;
+                            __stcs(reinterpret_cast<float4*>(T + ((long long)rb * m + i) * n + (long long)cb * m) + g, v);
+                        }
                     }
                 }
             }
@@ -225,14 +234,20 @@ extern "C" int ot_unfold_plan(int mode, int m, int N, const void* S_or_w, const 
         unfold_kernel<OT_PLAN_LOT, false><<<(int)grid, OT_BLOCK, 0, st>>>(
             m, N, (const float*)S_or_w, nullptr, nullptr, nullptr, nullptr, nullptr, kstar, 0.f, dense, T);
     else if (m % 4 == 0 && ((uintptr_t)T) % 16 == 0 && (!C_base || ((uintptr_t)C_base) % 16 == 0)) {
-        const long long nt4 = (long long)N * ((m + UT_R - 1) / UT_R) * ((m + UT_C4 - 1) / UT_C4);
+        // runs of rows sized for about 8 items per SM (at least one sub-tile)
+        const long long strips = (m + UT_C4 - 1) / UT_C4;
+        long long rpi = ((long long)N * strips * m + 8LL * sms - 1) / (8LL * sms);
+        rpi = (rpi + UT_R - 1) / UT_R * UT_R;
+        if (rpi < UT_R) rpi = UT_R;
+        const long long nt4 = (long long)N * strips * ((m + rpi - 1) / rpi);
         const int g4 = (int)(nt4 < (long long)sms * 8 ? nt4 : (long long)sms * 8);
         if (C_base)
             unfold_erot_vec4<false><<<g4, OT_BLOCK, 0, st>>>(m, N, (const double*)S_or_w, z, C_base, nullptr, nullptr,
-                                                            kappa, dense, T);
+                                                            kappa, dense, (int)rpi, T);
         else
             unfold_erot_vec4<true><<<g4, OT_BLOCK, 0, st>>>(m, N, (const double*)S_or_w, z, nullptr,
-                                                           (const float2*)x, (const float2*)y, kappa, dense, T);
+                                                           (const float2*)x, (const float2*)y, kappa, dense,
+                                                           (int)rpi, T);
     } else if (C_base)
         unfold_kernel<OT_PLAN_EROT, false><<<(int)grid, OT_BLOCK, 0, st>>>(
             m, N, nullptr, (const double*)S_or_w, z, C_base, nullptr, nullptr, nullptr, kappa, dense, T);

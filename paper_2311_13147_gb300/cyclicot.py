@@ -46,7 +46,7 @@ OT_OP_UNROLLED = 3
 OT_DEBUG_WITHHOLD_ARRIVAL = 1
 OT_DEBUG_TRACE = 2
 OT_DEBUG_NO_CLUSTER = 4
-OT_DEBUG_RING = 8
+OT_DEBUG_NO_RING = 8
 OT_STOP_L1_FULL = 0
 OT_STOP_L2_ROW = 1
 

@@ -356,7 +356,8 @@ def test_warm_start_resume(cy):
 
 
 def test_solver_variants_agree(cy):
-    """Bulk-reduce (one barrier per sweep), fused (two barriers) and two-pass solvers give the same iterate."""
+    """Ring (FP32 sweep), bulk-reduce (FP64 partials, one barrier per sweep), fused (two barriers) and
+    two-pass solvers give the same iterate."""
     p = I.image_grid_problem(side=32, seed=2, eps_frac=0.01)
     Cb = dev(p.C_base)
     G, _ = cy.ot_fold_cost(cy.OT_SOFTMIN, p.m, p.N, C_base=Cb, eps=p.eps)
@@ -366,9 +367,14 @@ def test_solver_variants_agree(cy):
     w2, z2, o2 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G,
                                         cy.options(p.eps, tol=1e-6, debug_flags=cy.OT_DEBUG_NO_CLUSTER))
     r2 = cy.read_result(o2)
-    assert r1["variant"] == "bulk" and r2["variant"] == "fused"
+    assert r1["variant"] == "ring" and r2["variant"] == "fused"
     assert abs(r1["iters"] - r2["iters"]) <= 1 and r1["status"] == r2["status"] == cy.OT_OK
     d = host(w1) - host(w2)
+    assert np.abs(d - d.mean()).max() <= 1e-6 * p.max_cost
+    w4, z4, o4 = cy.ot_sinkhorn_reduced(p.m, p.N, a, b, G, cy.options(p.eps, tol=1e-6, debug_flags=cy.OT_DEBUG_NO_RING))
+    r4 = cy.read_result(o4)
+    assert r4["variant"] == "bulk" and abs(r4["iters"] - r1["iters"]) <= 1 and r4["status"] == cy.OT_OK
+    d = host(w1) - host(w4)
     assert np.abs(d - d.mean()).max() <= 1e-6 * p.max_cost
     # odd size -> two-pass kernel on the same problem family
     q = I.sector_problem(97, 3, seed=1, eps_frac=0.02)
@@ -510,11 +516,12 @@ def test_paper_synthetic_erot_vs_oracle(cy, m, N):
 # ------------------------------------------------------------------ ring solver (per-thread copy ring, FP32 sweep)
 
 RING_CASES = [
-    (2100, 2, 0.05, 0, 0),      # > 2048 columns: default route, every band resident in shared memory
+    (2100, 2, 0.05, 0, 0),      # two warp groups x 16 columns per thread, every band resident
     (3000, 3, 0.02, 1, 0),      # 3000 columns: the copy ring streams the bands (ragged last chunk)
-    (4096, 2, 0.01, 2, 0),      # the widest route (8 columns per thread), streaming
-    (1024, 4, 0.01, 3, 8),      # forced (OT_DEBUG_RING): 256 threads, resident
-    (1500, 2, 0.02, 4, 8),      # forced: 512 threads x 4 columns, resident
+    (4096, 2, 0.01, 2, 0),      # the widest route, streaming
+    (1024, 4, 0.01, 3, 0),      # single-group ring kernel (256 threads), resident
+    (1500, 2, 0.02, 4, 0),      # two warp groups x 8 columns per thread, resident
+    (252, 3, 0.02, 5, 0),       # single-group, ragged (252 columns: most threads idle on the tail)
 ]
 
 

@@ -74,3 +74,19 @@ def test_static_scratch_odd_size_and_limit(cy):
     with pytest.raises(cy.OTError) as e:
         cy.ot_sinkhorn_reduced_static(m, 2, a, a, G, opt)
     assert e.value.code == cy.OT_ERR_UNSUPPORTED
+
+
+def test_static_scratch_at_the_size_limit(cy):
+    """m = 4096 (the widest resident-route size): the scratch the solver needs on this GPU fits the
+    4 MiB array, and the static entry point matches the workspace solver on two calls in a row."""
+    p = I.sector_problem(4096, 2, seed=4, eps_frac=0.05)
+    opt = cy.options(p.eps, tol=1e-6)
+    assert cy.ot_workspace_bytes(cy.OT_OP_SINKHORN_REDUCED, 4096, 2, opt) <= (4 << 20)
+    (w0, z0, ref), runs = _solve_both(cy, p)
+    assert ref["status"] == cy.OT_OK
+    for w, z, r in runs:
+        assert r["status"] == cy.OT_OK, r
+        assert abs(r["iters"] - ref["iters"]) <= 1
+        for x, x0 in ((w, w0), (z, z0)):
+            d = (x - x0).cpu().numpy()
+            assert np.abs(d - d.mean()).max() <= 1e-6 * p.max_cost
