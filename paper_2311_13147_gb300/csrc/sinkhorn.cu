@@ -1280,7 +1280,7 @@ __global__ void __launch_bounds__(NT, 1) sk_ring_kernel(SkArgs A) {
     unsigned epoch = 0;
 
     // ---- first copies: every band (resident) or the first S bands of the ring
-    long long issued = 0;
+    int ref_band = 0;   // band the next refill copies (wrapping)
     if (nbands > 0) {
         if (resident) {
             for (int b = 0; b < nbands; ++b) ring_issue<NT, CPT, R>(A, ring, b, r_beg, r_end, b);
@@ -1290,10 +1290,10 @@ __global__ void __launch_bounds__(NT, 1) sk_ring_kernel(SkArgs A) {
                 ring_issue<NT, CPT, R>(A, ring, s, r_beg, r_end, s % nbands);
                 cp_async_commit();
             }
-            issued = S;
+            ref_band = S % nbands;
         }
     }
-    long long consumed = 0;
+    int st_next = 0;    // stage read next (wrapping)
 
     __shared__ double s_dred[NW];
     double sa = 0.0, sb = 0.0;   // marginal sums (FP64, once per solve)
@@ -1361,13 +1361,15 @@ __global__ void __launch_bounds__(NT, 1) sk_ring_kernel(SkArgs A) {
             int st = b;
             if (!resident) {
                 cp_async_wait<S - 1>();
-                st = (int)(consumed % S);
+                st = st_next;
+                st_next = (st_next + 1 == S) ? 0 : st_next + 1;
             }
             const float* sbase = ring + (size_t)st * R * Nc;
             auto refill = [&]() {
                 if (!resident) {
-                    ring_issue<NT, CPT, R>(A, ring, st, r_beg, r_end, (int)(issued % nbands));
+                    ring_issue<NT, CPT, R>(A, ring, st, r_beg, r_end, ref_band);
                     cp_async_commit();
+                    ref_band = (ref_band + 1 == nbands) ? 0 : ref_band + 1;
                 }
             };
             auto none = []() {};
@@ -1379,7 +1381,6 @@ __global__ void __launch_bounds__(NT, 1) sk_ring_kernel(SkArgs A) {
             else
                 bad = ring_band<NT, CPT, R, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, ghi, cf, e, u, l1,
                                                           s_red[b & 1], refill);
-            if (!resident) { ++consumed; ++issued; }
             if (bad) {   // uniform over the block: redo the band max-shifted, its costs re-read from global memory
                 __syncthreads();   // (the ring stage may already hold the next band)
                 float dummy = 0.f;
@@ -1611,11 +1612,19 @@ __device__ __forceinline__ float warp_reduce_rows2(float (&v)[R], int lane) {
 // Copies of band `band` into stage `st` of group g (this thread's slots only).
 template <int CPT, int R>
 __device__ __forceinline__ void pp_issue(const SkArgs& A, float* gring, int st, int r_beg, int r_end, int band,
-                                         int gt, unsigned cvalid) {
+                                         int gt, unsigned cvalid, bool full_cols) {
     const int rb = r_beg + band * R;
     const int nr = min(R, r_end - rb);
     float* dst = gring + (size_t)st * R * A.Ncol + 4 * gt;
     const float* src = A.C + (long long)rb * A.ld + 4 * gt;
+    if (nr == R && full_cols) {   // the common case: no per-slot tests
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < CPT / 4; ++q)
+                cp_async16(dst + (size_t)r * A.Ncol + 4 * PP_G * q, src + (long long)r * A.ld + 4 * PP_G * q);
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (r < nr) {
@@ -1629,7 +1638,7 @@ __device__ __forceinline__ void pp_issue(const SkArgs& A, float* gring, int st, 
 // One band of up to R rows for group g.  SAFE: explicit max shift (first sweep, and
 // the rare redo when a row sum left the safe range); GSRC: costs from global memory.
 // Returns true when some row sum left the safe range (uniform over the group).
-template <int CPT, int R, bool SAFE, bool GSRC, typename Refill>
+template <int CPT, int R, bool SAFE, bool GSRC, bool FULL, typename Refill>
 __device__ __forceinline__ bool pp_band(const SkArgs& A, const RingRows& RS, const float* sb, long long rstride,
                                         int rb, int lb, int nr, int cur, int nxt, int g, int gt, unsigned cvalid,
                                         const pf2 (&gh)[CPT / 2], const pf2 (&cf)[CPT / 2], pf2 (&e)[R][CPT / 2],
@@ -1643,13 +1652,13 @@ __device__ __forceinline__ bool pp_band(const SkArgs& A, const RingRows& RS, con
     const bool writer = (lane & ((32 >> LOGR) - 1)) == 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const bool rv = r < nr;
+        const bool rv = FULL || r < nr;
         const float F = (SAFE || !rv) ? 0.f : RS.hi[cur * rm + lb + r];
         const pf2 FF = p2(F, F);
         const float* srow = sb + (rv ? r : 0) * rstride + 4 * gt;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            if (rv && (cvalid & (1u << q))) {
+            if (FULL || (rv && (cvalid & (1u << q)))) {
                 const float4 c = GSRC ? __ldg(reinterpret_cast<const float4*>(srow + 4 * PP_G * q))
                                       : *reinterpret_cast<const float4*>(srow + 4 * PP_G * q);
                 e[r][2 * q] = add_p2(fma_p2(p2(c.x, c.y), nk, gh[2 * q]), FF);
@@ -1793,18 +1802,23 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
     float2* gam2 = reinterpret_cast<float2*>(A.gc);   // [2][Ncol] published (hi, lo) per state
     unsigned epoch = 0;
 
-    // ---- first copies of this group's bands
-    long long issued = 0, consumed = 0;
+    // ---- first copies of this group's bands; then the stage to consume next and the
+    // band (of this group) the next refill copies, both as wrapping counters
+    // every thread of the block holds only valid columns: a block-uniform condition, so the
+    // fast path (which holds warp-synchronous shuffles) is taken by whole groups or not at all
+    const bool full_cols = Nc == 4 * PP_G * NV;
+    int st_next = 0, ref_band = 0;
     if (gbands > 0) {
         if (resident) {
-            for (int bb = 0; bb < gbands; ++bb) pp_issue<CPT, R>(A, gring, bb, r_beg, r_end, 2 * bb + g, gt, cvalid);
+            for (int bb = 0; bb < gbands; ++bb)
+                pp_issue<CPT, R>(A, gring, bb, r_beg, r_end, 2 * bb + g, gt, cvalid, full_cols);
             cp_async_commit();
         } else {
             for (int s = 0; s < S; ++s) {
-                pp_issue<CPT, R>(A, gring, s, r_beg, r_end, 2 * (s % gbands) + g, gt, cvalid);
+                pp_issue<CPT, R>(A, gring, s, r_beg, r_end, 2 * (s % gbands) + g, gt, cvalid, full_cols);
                 cp_async_commit();
             }
-            issued = S;
+            ref_band = S % gbands;
         }
     }
 
@@ -1881,30 +1895,34 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
             int st = bb;
             if (!resident) {
                 cp_async_wait<S - 1>();
-                st = (int)(consumed % S);
+                st = st_next;
+                st_next = (st_next + 1 == S) ? 0 : st_next + 1;
             }
             const float* sbase = gring + (size_t)st * R * Nc;
             auto refill = [&]() {
                 if (!resident) {
-                    pp_issue<CPT, R>(A, gring, st, r_beg, r_end, 2 * (int)(issued % gbands) + g, gt, cvalid);
+                    pp_issue<CPT, R>(A, gring, st, r_beg, r_end, 2 * ref_band + g, gt, cvalid, full_cols);
                     cp_async_commit();
+                    ref_band = (ref_band + 1 == gbands) ? 0 : ref_band + 1;
                 }
             };
             auto none = []() {};
             float u[R];
             bool bad;
             if (t == 1)
-                bad = pp_band<CPT, R, true, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf, e, u,
-                                                   l1, s_red[g][bb & 1], refill);
+                bad = pp_band<CPT, R, true, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf,
+                                                          e, u, l1, s_red[g][bb & 1], refill);
+            else if (nr == R && full_cols)
+                bad = pp_band<CPT, R, false, false, true>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf,
+                                                          e, u, l1, s_red[g][bb & 1], refill);
             else
-                bad = pp_band<CPT, R, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf, e,
-                                                    u, l1, s_red[g][bb & 1], refill);
-            if (!resident) { ++consumed; ++issued; }
+                bad = pp_band<CPT, R, false, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh,
+                                                           cf, e, u, l1, s_red[g][bb & 1], refill);
             if (bad) {   // uniform over the group: redo the band max-shifted from the costs in global memory
                 group_sync(g);
                 float dummy = 0.f;
-                if (pp_band<CPT, R, true, true>(A, RS, A.C + (long long)rb * A.ld, A.ld, rb, lb, nr, cur, nxt, g, gt,
-                                                cvalid, gh, cf, e, u, dummy, s_red[g][bb & 1], none))
+                if (pp_band<CPT, R, true, true, false>(A, RS, A.C + (long long)rb * A.ld, A.ld, rb, lb, nr, cur, nxt, g,
+                                                       gt, cvalid, gh, cf, e, u, dummy, s_red[g][bb & 1], none))
                     if (gt == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
                 group_sync(g);
             }
