@@ -1641,7 +1641,7 @@ __device__ __forceinline__ void pp_issue(const SkArgs& A, float* gring, int st, 
 template <int CPT, int R, bool SAFE, bool GSRC, bool FULL, typename Refill>
 __device__ __forceinline__ bool pp_band(const SkArgs& A, const RingRows& RS, const float* sb, long long rstride,
                                         int rb, int lb, int nr, int cur, int nxt, int g, int gt, unsigned cvalid,
-                                        const pf2 (&gh)[CPT / 2], const pf2 (&cf)[CPT / 2], pf2 (&e)[R][CPT / 2],
+                                        const pf2 (&gh)[CPT / 2], const pf2* __restrict__ scf, pf2 (&e)[R][CPT / 2],
                                         float (&u)[R], float& l1, float (*s_red)[8], Refill refill) {
     constexpr int NV = CPT / 4;
     const int lane = gt & 31, wg = gt >> 5;
@@ -1705,6 +1705,9 @@ __device__ __forceinline__ bool pp_band(const SkArgs& A, const RingRows& RS, con
         group_sync(g);   // s_red is reused for the sums below
     }
     float ps[R];
+    pf2 cf[CPT / 2];   // the column factors 2^lo, read from shared memory for this band only
+#pragma unroll
+    for (int q = 0; q < CPT / 2; ++q) cf[q] = scf[q * PP_G + gt];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         pf2 s2 = p2(0.f, 0.f);
@@ -1789,6 +1792,8 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
     unsigned char* p = dsm + align256_hd(2 * gring_floats * sizeof(float));
     float* s_acc = reinterpret_cast<float*>(p);                 // [PP_G][CPT]
     p += align256_hd((size_t)PP_G * CPT * sizeof(float));
+    pf2* s_cf = reinterpret_cast<pf2*>(p);                      // [CPT / 2][PP_G] column factors 2^lo
+    p += align256_hd((size_t)PP_G * CPT * sizeof(float));
     RingRows RS;
     RS.hi = reinterpret_cast<float*>(p);
     RS.lo = RS.hi + 2 * A.rows_max;
@@ -1842,7 +1847,7 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
     const double inv_sa = 1.0 / tsa, inv_sb = 1.0 / tsb;
     for (int li = tid; li < r_end - r_beg; li += NT) RS.alpha[li] = (float)((double)A.a[r_beg + li] * inv_sa);
     // potentials of this thread's columns, and the owned columns' full state
-    pf2 gh[CPT / 2], cf[CPT / 2];
+    pf2 gh[CPT / 2];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         float hv[4], cv[4];
@@ -1856,8 +1861,10 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
         }
         gh[2 * q] = p2(hv[0], hv[1]);
         gh[2 * q + 1] = p2(hv[2], hv[3]);
-        cf[2 * q] = p2(cv[0], cv[1]);
-        cf[2 * q + 1] = p2(cv[2], cv[3]);
+        if (g == 0) {
+            s_cf[(2 * q) * PP_G + gt] = p2(cv[0], cv[1]);
+            s_cf[(2 * q + 1) * PP_G + gt] = p2(cv[2], cv[3]);
+        }
     }
     if (tid < nown) {
         const int j = o_beg + tid;
@@ -1910,19 +1917,19 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
             float u[R];
             bool bad;
             if (t == 1)
-                bad = pp_band<CPT, R, true, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf,
+                bad = pp_band<CPT, R, true, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, s_cf,
                                                           e, u, l1, s_red[g][bb & 1], refill);
             else if (nr == R && full_cols)
-                bad = pp_band<CPT, R, false, false, true>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, cf,
+                bad = pp_band<CPT, R, false, false, true>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh, s_cf,
                                                           e, u, l1, s_red[g][bb & 1], refill);
             else
                 bad = pp_band<CPT, R, false, false, false>(A, RS, sbase, Nc, rb, lb, nr, cur, nxt, g, gt, cvalid, gh,
-                                                           cf, e, u, l1, s_red[g][bb & 1], refill);
+                                                           s_cf, e, u, l1, s_red[g][bb & 1], refill);
             if (bad) {   // uniform over the group: redo the band max-shifted from the costs in global memory
                 group_sync(g);
                 float dummy = 0.f;
                 if (pp_band<CPT, R, true, true, false>(A, RS, A.C + (long long)rb * A.ld, A.ld, rb, lb, nr, cur, nxt, g,
-                                                       gt, cvalid, gh, cf, e, u, dummy, s_red[g][bb & 1], none))
+                                                       gt, cvalid, gh, s_cf, e, u, dummy, s_red[g][bb & 1], none))
                     if (gt == 0) set_status(A.ctrl, OT_ERR_NONFINITE);
                 group_sync(g);
             }
@@ -1963,30 +1970,40 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
         if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
         trace_mark(A, t, 2);
 
-        // ---- owner phase: the row L1 of the state after t - 1 iterations (same order in every block),
-        // then the owned columns' sums over all blocks (compensated FP32, fixed order)
-        if (wid == 0) {
-            float s = 0.f, c = 0.f;
-            for (int b2 = lane; b2 < G; b2 += 32) kahan_add(s, c, __ldcg(reinterpret_cast<const float*>(A.l1part) + b2));
-            s -= c;
-            s = warp_sum(s);
-            if (lane == 0) s_L1 = s;
-        }
+        // ---- owner phase: the owned columns' sums over all blocks (compensated FP32, fixed order)
+        // and the row L1 of the state after t - 1 iterations (the last warp, same order in every
+        // block); every load is issued before any arithmetic
         {
             const int c = tid & 31, sl = tid >> 5;   // column of the owned range, slice of the blocks
-            float s = 0.f, cp = 0.f;
-            if (c < nown) {
-                float v[10];
+            float v[10], lv[5];
 #pragma unroll
-                for (int k = 0; k < 10; ++k) {
-                    const int b2 = sl + 16 * k;
-                    v[k] = (b2 < G) ? __ldcg(A.part + (long long)b2 * A.pstride + o_beg + c) : 0.f;
-                }
-                for (int k = 0; k < 10; ++k) kahan_add(s, cp, v[k]);
-                for (int b2 = sl + 160; b2 < G; b2 += 16) kahan_add(s, cp, __ldcg(A.part + (long long)b2 * A.pstride + o_beg + c));
+            for (int k = 0; k < 10; ++k) {
+                const int b2 = sl + 16 * k;
+                v[k] = (c < nown && b2 < G) ? __ldcg(A.part + (long long)b2 * A.pstride + o_beg + c) : 0.f;
             }
+            if (wid == NW - 1) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int b2 = lane + 32 * k;
+                    lv[k] = (b2 < G) ? __ldcg(reinterpret_cast<const float*>(A.l1part) + b2) : 0.f;
+                }
+            }
+            float s = 0.f, cp = 0.f;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) kahan_add(s, cp, v[k]);
+            if (c < nown)
+                for (int b2 = sl + 160; b2 < G; b2 += 16) kahan_add(s, cp, __ldcg(A.part + (long long)b2 * A.pstride + o_beg + c));
             s_own[sl][0][c] = s;
             s_own[sl][1][c] = cp;
+            if (wid == NW - 1) {
+                float ls = 0.f, lc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) kahan_add(ls, lc, lv[k]);
+                for (int b2 = lane + 160; b2 < G; b2 += 32) kahan_add(ls, lc, __ldcg(reinterpret_cast<const float*>(A.l1part) + b2));
+                ls -= lc;
+                ls = warp_sum(ls);
+                if (lane == 0) s_L1 = ls;
+            }
         }
         __syncthreads();
         const float L1 = s_L1;
@@ -2015,27 +2032,40 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
             }
             break;
         }
-        if (wid == 0 && lane < nown) {
+        // half-warp h (of warps 0..15) combines the 16 slices of owned column c = h with TwoSum merges
+        // (fixed tree, the same in every block), then its lane 0 updates the column's potential
+        {
+            const int c = tid >> 4, sl = tid & 15;
             float s = 0.f, cp = 0.f;
-#pragma unroll
-            for (int sl = 0; sl < 16; ++sl) {
-                kahan_add(s, cp, s_own[sl][0][lane]);
-                kahan_add(s, cp, -s_own[sl][1][lane]);
+            if (c < nown) {
+                s = s_own[sl][0][c];
+                cp = s_own[sl][1][c];
             }
-            s -= cp;
-            const float Rj = s * s_ocf[lane];   // column sum of the plan after the row update
-            if (Rj != Rj) {
-                set_status(A.ctrl, OT_ERR_NONFINITE);
-            } else if (Rj > 1e-30f && Rj < 1e30f) {
-                float hi = s_ohi[lane], lo = s_olo[lane];
-                df_sub(hi, lo, lg2(__fdividef(Rj, s_obt[lane])));
-                s_ohi[lane] = hi;
-                s_olo[lane] = lo;
-                s_ocf[lane] = ex2(lo);
-                gam2[nxt * Nc + o_beg + lane] = make_float2(hi, lo);
-            } else {
-                atomicAdd(&s_fix, 1);
-                s_ohi[lane] = NAN;   // marks the column for the fallback below
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {   // (s, cp) + partner's: exact sum of the two hi parts
+                const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, cp, o);
+                const float t = s + s2;
+                const float bb = t - s;
+                const float err = (s - (t - bb)) + (s2 - bb);
+                cp = cp + c2 - err;
+                s = t;
+            }
+            if (sl == 0 && c < nown) {
+                s -= cp;
+                const float Rj = s * s_ocf[c];   // column sum of the plan after the row update
+                if (Rj != Rj) {
+                    set_status(A.ctrl, OT_ERR_NONFINITE);
+                } else if (Rj > 1e-30f && Rj < 1e30f) {
+                    float hi = s_ohi[c], lo = s_olo[c];
+                    df_sub(hi, lo, lg2(__fdividef(Rj, s_obt[c])));
+                    s_ohi[c] = hi;
+                    s_olo[c] = lo;
+                    s_ocf[c] = ex2(lo);
+                    gam2[nxt * Nc + o_beg + c] = make_float2(hi, lo);
+                } else {
+                    atomicAdd(&s_fix, 1);
+                    s_ohi[c] = NAN;   // marks the column for the fallback below
+                }
             }
         }
         __syncthreads();
@@ -2057,18 +2087,24 @@ __global__ void __launch_bounds__(2 * PP_G, 1) sk_pp_kernel(SkArgs A) {
         }
         trace_mark(A, t, 6);
         if (!grid_sync(A.ctrl, G, A.timeout_ns, epoch)) { go = false; break; }
-        // ---- every thread: the new potentials of its columns
+        // ---- every thread: the new potentials of its columns (every slot is redefined, so the old
+        // values are not kept alive through the exchange)
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
+            float4 h01 = make_float4(0.f, 0.f, 0.f, 0.f), h23 = h01;
             if (cvalid & (1u << q)) {
                 const float4* src = reinterpret_cast<const float4*>(gam2 + nxt * Nc + 4 * (gt + PP_G * q));
-                const float4 h01 = __ldcg(src), h23 = __ldcg(src + 1);   // (hi, lo) of 4 columns
-                gh[2 * q] = p2(h01.x, h01.z);
-                gh[2 * q + 1] = p2(h23.x, h23.z);
-                cf[2 * q] = p2(ex2(h01.y), ex2(h01.w));
-                cf[2 * q + 1] = p2(ex2(h23.y), ex2(h23.w));
+                h01 = __ldcg(src);   // (hi, lo) of 4 columns
+                h23 = __ldcg(src + 1);
+            }
+            gh[2 * q] = p2(h01.x, h01.z);
+            gh[2 * q + 1] = p2(h23.x, h23.z);
+            if (g == 0) {
+                s_cf[(2 * q) * PP_G + gt] = p2(ex2(h01.y), ex2(h01.w));
+                s_cf[(2 * q + 1) * PP_G + gt] = p2(ex2(h23.y), ex2(h23.w));
             }
         }
+        __syncthreads();   // the column factors are read by both groups in the next sweep
         trace_mark(A, t, 3);
     }
     if (!args_ok) {
@@ -2490,7 +2526,7 @@ static int launch_pp_t(SkArgs& A, int grid, cudaStream_t st) {
     if ((A.Ncol + grid - 1) / grid > 32) return OT_ERR_UNSUPPORTED;   // owned columns per block
     const int nb_max = (A.rows_max + R - 1) / R;
     const size_t band_bytes = (size_t)R * A.Ncol * sizeof(float);
-    const size_t state = align256_hd((size_t)PP_G * CPT * sizeof(float)) +
+    const size_t state = 2 * align256_hd((size_t)PP_G * CPT * sizeof(float)) +
                          align256_hd((size_t)A.rows_max * 7 * sizeof(float)) + 4 * 32 * sizeof(float);
     const size_t limit = 227 * 1024 - 8192;   // the opt-in maximum less the kernel's static shared memory
     const size_t res_bytes = align256_hd(2 * (size_t)((nb_max + 1) / 2) * band_bytes);
@@ -2505,7 +2541,7 @@ static int launch_pp_t(SkArgs& A, int grid, cudaStream_t st) {
 static int launch_ring(SkArgs& A, int grid, cudaStream_t st) {
     if (A.Ncol <= 1024) return launch_ring_t<256, 4, 8, 3>(A, grid, st);
     if (A.Ncol <= 2048) return launch_pp_t<8, 4, 3>(A, grid, st);
-    return launch_pp_t<16, 2, 3>(A, grid, st);
+    return launch_pp_t<16, 2, 2>(A, grid, st);
 }
 
 size_t batch_single_ws_bytes(int m);
