@@ -526,7 +526,7 @@ def run_ours_batch(args, rank, world, local_rank):
     alg_bytes = float(sum(4.0 * d.m * d.ld * (r["iters"] + 1) for d, r in zip(bs.descs, res)))
     achieved = alg_bytes / (solve_ms / 1e3) / 1e9
     peaks, peak_src = load_peaks()
-    traffic = profile_traffic("batch_solve_kernel.batch512.md", "batch.cu")
+    traffic = None   # DRAM counters are captured on a 64-problem case only (profiles/batch_solve_kernel.batch512.md)
     # e2e through the public API: host inputs (pinned) in, potentials and results out, every step
     h_pts = bs.points.cpu().pin_memory()
     h_a = bs.a.cpu().pin_memory()
@@ -937,7 +937,8 @@ def run_ours_polar(args, rank, world, local_rank):
         "sweep": {"reduced_solve_ms": solve_ms, "solver": variant, "sweeps": sweeps,
                   "us_per_sweep": solve_ms * 1e3 / sweeps, "alg_gbs": gbs},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "frac": gbs / peaks["hbm_gbs"],
+                     "traffic": profile_traffic("sk_pp_kernel.polar_m4096.md", "sinkhorn.cu"),
                      "peak_source": (peak_src + " (MEASURED_PEAKS.json hbm_gbs)") if peak_src == "measured"
                      else peak_src + " (6.8 TB/s)",
                      "kernel": f"reduced solver ({variant}), 4 m^2 bytes of the folded cost per sweep",
