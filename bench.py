@@ -736,9 +736,9 @@ def run_ours_precision(args, rank, world, local_rank):
                      "tensor_tflops": tflops,
                      "tensor_frac_of_bf16_peak": tflops / peaks.get("bf16_tflops", 1900.0),
                      "ms_per_bf16_iter": per_iter_ms},
-        # per cost and step: the fold, the kernel-domain solve (K and K^T, prep, 4 launches per
-        # BF16 iteration, the log of the scalings) and the polish
-        "gpu_launches": args.steps * len(sbs) * (1 + 3 + 4 * PRECISION_BF16_ITERS + 1),
+        # per cost and step: the fold, the kernel-domain solve (K and K^T, prep, 2 launches per
+        # BF16 iteration (each product applies its scaling update), the log of the scalings) and the polish
+        "gpu_launches": args.steps * len(sbs) * (1 + 3 + 2 * PRECISION_BF16_ITERS + 1),
         "clocks": clk,
     }
     # objective errors against the FP64 oracle on the two smallest costs (4 pairs each)

@@ -12,16 +12,21 @@
 // z = eps log V (warm start) to the requested tolerance.
 //
 // GEMM kernel (one 128-row tile of the output and one slice of the reduction
-// per CTA, 128 threads):
+// per CTA, 128 threads; the slices of a tile form one thread-block cluster):
 //   thread 0      TMA producer: K tile [128 x 64] and scaling tile [64 x 64]
 //                 per 64-wide reduction block into a 4-stage ring (128-byte
 //                 swizzle), completion counted on the stage's mbarrier;
 //   thread 32     MMA issuer: 4 tcgen05.mma (M 128, N 64, K 16, BF16 -> FP32)
 //                 per stage, then tcgen05.commit frees the stage;
 //   all 4 warps   epilogue: tcgen05.ld of the 128 x 64 FP32 accumulator (warp w
-//                 reads lanes 32w..32w+31), stored as this reduction slice's
-//                 partial product [64][mp] (one row per right-hand side); the
-//                 scaling update sums the slices.
+//                 reads lanes 32w..32w+31) into this CTA's shared memory (the
+//                 free pipeline stages); after a cluster barrier, CTA r of the
+//                 cluster sums the slices of its share of the 64 right-hand
+//                 sides from its peers' shared memory (distributed shared
+//                 memory, slices in order) and writes either the product or,
+//                 in the solver, the scaling update X = H ./ D of those columns;
+//                 a second cluster barrier keeps every slice readable until
+//                 its peers are done.  No partial product touches global memory.
 // Every wait is bounded; an expired wait sets an error flag and the CTA still
 // frees its tensor memory.
 #include <cuda.h>
@@ -43,7 +48,7 @@ int device_sms();
 #define KD_B_BYTES (KD_BN * KD_BK * 2)
 #define KD_STAGE_BYTES (KD_A_BYTES + KD_B_BYTES)
 #define KD_SMEM (KD_STAGES * KD_STAGE_BYTES + 1024)
-#define KD_MAX_SPLITS 16           // reduction slices (each stores its own partial product)
+#define KD_MAX_SPLITS 8            // reduction slices = cluster size (portable limit), a power of two
 
 // ---- tcgen05 / TMA helpers (inline PTX)
 
@@ -64,6 +69,39 @@ __device__ __forceinline__ void tmem_alloc(unsigned* slot, unsigned ncols) {
 __device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+
+// Cluster barrier (every thread of every CTA of the cluster arrives); release and
+// acquire order the shared-memory writes before it with the peer reads after it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// The address of the same shared-memory location in CTA `rank` of this cluster.
+__device__ __forceinline__ unsigned dsmem_addr(unsigned local, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+// (volatile: stays after the cluster barrier; no memory clobber, so the loads of a
+// chunk can all be in flight together)
+__device__ __forceinline__ float ld_dsmem(unsigned addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+// Programmatic dependent launch: wait until the preceding grid of the stream has
+// completed and its writes are visible (returns at once without a preceding
+// dependent-launch edge); allow the next grid to begin launching.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -113,29 +151,39 @@ __device__ __forceinline__ unsigned long long smem_desc_sw128(const void* tile) 
 
 struct GemmArgs {
     int mp;                       // padded size (multiple of 128)
-    int kb_per_split;             // reduction blocks (of 64) per CTA slice
-    float* Dp;                    // [splits][64][mp] partial products, one slice per blockIdx.y
     int* err;                     // error flag (OT_ERR_TIMEOUT on an expired wait)
     unsigned long long timeout_ns;
+    float* D;                     // [64][mp] product output (H == nullptr)
+    // scaling update (H != nullptr): X = H ./ D, 0 where D = 0, H = 0 or i >= m
+    const float* H;               // [64][mp] target histograms (alpha or beta)
+    float* X;                     // [64][mp] scaling, updated in place (U or V)
+    __nv_bfloat16* Xt;            // [64][mp] its BF16 copy, the next product's operand
+    float* row_err;               // [64] += sum_i |Xold_i D_i - H_i| (the state before the update), or nullptr
+    int m;                        // problem size (rows >= m are padding)
 };
 
-// Dp[s][n][i] = sum over slice s of k of A[i][k] X[n][k] for this CTA's rows i.
+// D[n][i] = sum_k A[i][k] X[n][k] for this cluster's 128 rows i, reduced over the
+// cluster's slices of k, then written or turned into the scaling update.
 // A: tensor map of a [mp][mp] BF16 matrix (row-major, K-major operand);
 // X: tensor map of the [64][mp] BF16 scaling vectors (K-major operand).
+// Grid (mp / 128, splits), cluster (1, splits, 1); slice y covers reduction
+// blocks [y nkb / splits, (y + 1) nkb / splits), never empty (splits <= nkb).
+template <int SPLITS>
 __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmX, GemmArgs g) {
     extern __shared__ unsigned char kd_smem_raw[];
     __shared__ __align__(8) unsigned long long full[KD_STAGES], empty[KD_STAGES], accb;
     __shared__ unsigned tmem_slot;
     __shared__ int s_issued;
+    __shared__ float s_err[KD_BN];
     unsigned char* base =
         (unsigned char*)(((uintptr_t)kd_smem_raw + 1023) & ~(uintptr_t)1023);   // 1024-byte aligned tiles
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * KD_BM;
-    const int nkb_total = g.mp / KD_BK;
-    const int kb0 = blockIdx.y * g.kb_per_split;
-    const int kb1 = min(nkb_total, kb0 + g.kb_per_split);
-    const int nkb = kb1 - kb0;   // >= 1 (the host sizes the split)
+    const int nkb_total = g.mp / KD_BK, splits = SPLITS;
+    const int kb0 = (int)((blockIdx.y * nkb_total) / splits);
+    const int kb1 = (int)(((blockIdx.y + 1) * nkb_total) / splits);
+    const int nkb = kb1 - kb0;   // >= 1 (the host keeps splits <= nkb_total)
 
     if (tid == 0) {
         for (int s = 0; s < KD_STAGES; ++s) {
@@ -145,15 +193,31 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
         mbar_init(&accb, 1);
         fence_mbar_init();
     }
+    if (tid < KD_BN) s_err[tid] = 0.f;
     if (warp == 1) tmem_alloc(&tmem_slot, KD_BN);   // 64 FP32 columns x 128 lanes
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = tmem_slot;
 
+    // a launch queued behind this one (programmatic dependent launch) may start its own
+    // prologue now; it reads nothing this grid writes before its griddepcontrol.wait
+    grid_dep_launch();
+
     if (warp == 0 && lane == 0) {
-        // producer
-        int i = 0;
+        // producer.  The matrix tiles of the first stages depend on no earlier launch of
+        // the solve (K and K^T are written once, before the first product, which is
+        // launched without the dependent-launch attribute): they are requested before
+        // waiting for the previous product, whose scaling update the X tiles read.
+        const int pre = min(nkb, KD_STAGES);
+        for (int i = 0; i < pre; ++i) {
+            mbar_arrive_expect_tx(&full[i], KD_STAGE_BYTES);
+            tma_load_2d(base + (size_t)i * KD_STAGE_BYTES, &tmA, (kb0 + i) * KD_BK, m0, &full[i]);
+        }
+        grid_dep_wait();
+        for (int i = 0; i < pre; ++i)
+            tma_load_2d(base + (size_t)i * KD_STAGE_BYTES + KD_A_BYTES, &tmX, (kb0 + i) * KD_BK, 0, &full[i]);
+        int i = pre;
         for (; i < nkb; ++i) {
             const int s = i % KD_STAGES;
             const unsigned ph = (unsigned)((i / KD_STAGES) & 1);
@@ -194,24 +258,24 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
     __syncwarp();
 
     // epilogue: 128 rows x 64 columns from tensor memory
+    grid_dep_wait();   // the previous launch's writes are visible before H, X and D are touched
+    // this CTA's share of the right-hand sides, n in [n0, n0 + NPER), in chunks of CH
+    constexpr int NPER = KD_BN / SPLITS, CH = NPER < 32 ? NPER : 32;
+    const int n0 = (int)blockIdx.y * NPER;   // blockIdx.y is the rank in the cluster
+    const int i = m0 + tid;
+    float h[CH], xo[CH];   // the first chunk's histogram and old scaling, fetched while the MMAs run
+    if (g.H) {
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const size_t o = (size_t)(n0 + j) * g.mp + i;
+            h[j] = g.H[o];
+            xo[j] = g.row_err ? g.X[o] : 0.f;
+        }
+    }
     const bool ok = mbar_wait(&accb, 0u, g.timeout_ns);
     if (!ok && lane == 0) atomicExch(g.err, OT_ERR_TIMEOUT);
     tc_fence_after();
-    if (__all_sync(0xffffffffu, ok)) {
-        const int row = m0 + 32 * warp + lane;
-        const unsigned taddr = tmem + ((unsigned)(32 * warp) << 16);
-#pragma unroll
-        for (int c = 0; c < KD_BN / 16; ++c) {
-            float v[16];
-            tmem_ld16(taddr + 16 * c, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                g.Dp[((size_t)blockIdx.y * KD_BN + 16 * c + j) * g.mp + row] = v[j];   // coalesced over lanes
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    // copies still in flight (only after an expired wait) must land before the CTA exits
+    // copies still in flight (only after an expired wait) land before the stages are reused
     if (tid == 0) {
         const int issued = s_issued;
         for (int s = 0; s < KD_STAGES && s < issued; ++s) {
@@ -219,10 +283,77 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
             mbar_wait(&full[s], (unsigned)((last / KD_STAGES) & 1), g.timeout_ns);
         }
     }
+    __syncthreads();   // every MMA has read its stage (accb) and every copy has landed
+    // this slice's partial product, [64][128] FP32 in the first 32 KB of the stages
+    float* part = reinterpret_cast<float*>(base);
+    {
+        const bool all_ok = __all_sync(0xffffffffu, ok);
+        const unsigned taddr = tmem + ((unsigned)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < KD_BN / 16; ++c) {
+            float v[16];
+            if (all_ok) {
+                tmem_ld16(taddr + 16 * c, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) part[(16 * c + j) * KD_BM + tid] = v[j];   // conflict-free over lanes
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, KD_BN);
     }
+    cluster_sync();   // every slice of the tile is in its CTA's shared memory
+
+    const unsigned part_local = smem_addr(part + tid);
+#pragma unroll 1
+    for (int nc = 0; nc < NPER; nc += CH) {
+        if (nc > 0 && g.H) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const size_t o = (size_t)(n0 + nc + j) * g.mp + i;
+                h[j] = g.H[o];
+                xo[j] = g.row_err ? g.X[o] : 0.f;
+            }
+        }
+        // every slice's values first (all loads in flight), then the sums in slice order
+        float v[SPLITS][CH];
+#pragma unroll
+        for (int sl = 0; sl < SPLITS; ++sl) {
+            const unsigned pa = dsmem_addr(part_local, (unsigned)sl) + (unsigned)((n0 + nc) * KD_BM * 4);
+#pragma unroll
+            for (int j = 0; j < CH; ++j) v[sl][j] = ld_dsmem(pa + (unsigned)(j * KD_BM * 4));
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            float d = 0.f;
+#pragma unroll
+            for (int sl = 0; sl < SPLITS; ++sl) d += v[sl][j];
+            const int n = n0 + nc + j;
+            const size_t o = (size_t)n * g.mp + i;
+            if (!g.H) {
+                g.D[o] = d;
+                continue;
+            }
+            const float x = (i < g.m && d > 0.f && h[j] > 0.f) ? __fdiv_rn(h[j], d) : 0.f;
+            if (g.row_err) {
+                const float e = warp_sum(fabsf(fmaf(xo[j], d, -h[j])));
+                if (lane == 0 && e != 0.f) atomicAdd(&s_err[n], e);
+            }
+            g.X[o] = x;
+            g.Xt[o] = __float2bfloat16_rn(x);
+        }
+    }
+    if (g.row_err) {
+        __syncthreads();
+        if (tid < NPER && s_err[n0 + tid] != 0.f) atomicAdd(g.row_err + n0 + tid, s_err[n0 + tid]);
+    }
+    cluster_sync();   // the peers have read this CTA's slice
 }
 
 // K = exp(-G / eps) (log2 form: 2^(-G kap)), BF16, and its transpose; zero padding.
@@ -282,31 +413,6 @@ __global__ void __launch_bounds__(256) kd_prep_kernel(const float* __restrict__ 
     }
 }
 
-// X = H ./ D with D the sum of the product's reduction slices (0 where D = 0 or
-// outside the problem); err[n] += sum_i |Xold_i D_i - H_i|,
-// the L1 marginal error of the state before this half-iteration on this side.
-__global__ void __launch_bounds__(256) kd_scale_kernel(const float* __restrict__ Dp, int splits,
-                                                       const float* __restrict__ H, float* __restrict__ X,
-                                                       __nv_bfloat16* __restrict__ Xt, int m, int mp,
-                                                       float* __restrict__ err) {
-    const int n = blockIdx.y;
-    float e = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x) {
-        const size_t o = (size_t)n * mp + i;
-        float d = 0.f;   // the product: sum of the reduction slices
-        for (int sl = 0; sl < splits; ++sl) d += Dp[(size_t)sl * KD_BN * mp + o];
-        const float h = H[o];
-        if (err) e += fabsf(fmaf(X[o], d, -h));
-        const float x = (i < m && d > 0.f && h > 0.f) ? __fdiv_rn(h, d) : 0.f;
-        X[o] = x;
-        Xt[o] = __float2bfloat16_rn(x);
-    }
-    if (err) {
-        e = warp_sum(e);
-        if ((threadIdx.x & 31) == 0 && e != 0.f) atomicAdd(err + n, e);
-    }
-}
-
 // z = eps ln V (FP64 out, [nrhs][m]); zero scalings map to the most negative finite log.
 __global__ void __launch_bounds__(256) kd_log_kernel(const float* __restrict__ V, int m, int mp, int nrhs, double eps,
                                                      double* __restrict__ z) {
@@ -323,7 +429,7 @@ __global__ void __launch_bounds__(256) kd_log_kernel(const float* __restrict__ V
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct KdLayout {
-    size_t K, Kt, alpha, beta, U, V, Ut, Vt, D, err, flag, total;
+    size_t K, Kt, alpha, beta, U, V, Ut, Vt, err, flag, total;
 };
 
 static KdLayout kd_layout(int mp) {
@@ -338,7 +444,6 @@ static KdLayout kd_layout(int mp) {
     L.V = o; o = a256(o + 4 * vn);
     L.Ut = o; o = a256(o + 2 * vn);
     L.Vt = o; o = a256(o + 2 * vn);
-    L.D = o; o = a256(o + 4 * vn * KD_MAX_SPLITS);
     L.err = o; o = a256(o + 4 * (size_t)KD_BN);
     L.flag = o; o = a256(o + 64);
     L.total = o;
@@ -378,32 +483,63 @@ static bool make_map(CUtensorMap* map, void* base, int rows, int cols, int box_r
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Reduction slices of the product for size mp (the grid fills two resident CTAs per SM in one wave).
+// Reduction slices of the product for size mp: the largest power of two <= 8 that keeps
+// the grid within two resident CTAs per SM (one wave) and every slice non-empty.
 static int kd_splits(int mp) {
     const int sms = device_sms();
     if (sms <= 0) return 0;
     const int tiles = mp / KD_BM, nkb = mp / KD_BK;
-    int splits = (2 * sms) / tiles;
-    splits = splits < 1 ? 1 : (splits > nkb ? nkb : splits);
-    splits = splits > KD_MAX_SPLITS ? KD_MAX_SPLITS : splits;
-    const int per = (nkb + splits - 1) / splits;
-    return (nkb + per - 1) / per;   // every slice non-empty
+    int splits = 1;
+    while (splits * 2 <= KD_MAX_SPLITS && splits * 2 <= nkb && tiles * splits * 2 <= 2 * sms) splits *= 2;
+    return splits;
 }
 
-// Partial products Dp[s] (s < kd_splits(mp)) of A X^T for the [mp][mp] BF16 matrix behind mapA.
-static int kd_gemm(const CUtensorMap& mapA, const CUtensorMap& mapX, int mp, float* Dp, int* flag,
-                   unsigned long long timeout_ns, cudaStream_t st) {
+// One product of the [mp][mp] BF16 matrix behind mapA with the scalings behind mapX:
+// g.H == nullptr writes D = A X^T to g.D, else the scaling update (g's other fields).
+// pdl: launch as a programmatic dependent of the previous kernel in the stream, which must
+// not write mapA's matrix (the previous product of the solve).
+static int kd_gemm(const CUtensorMap& mapA, const CUtensorMap& mapX, int mp, GemmArgs g, int* flag,
+                   unsigned long long timeout_ns, cudaStream_t st, bool pdl = false) {
     const int splits = kd_splits(mp);
     if (splits <= 0) return OT_ERR_CUDA;
-    const int tiles = mp / KD_BM, nkb = mp / KD_BK;
-    GemmArgs g;
     g.mp = mp;
-    g.kb_per_split = (nkb + splits - 1) / splits;
-    g.Dp = Dp;
     g.err = flag;
     g.timeout_ns = timeout_ns;
-    kd_gemm_kernel<<<dim3(tiles, splits), 128, KD_SMEM, st>>>(mapA, mapX, g);
-    return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(mp / KD_BM, splits, 1);
+    cfg.blockDim = dim3(128, 1, 1);
+    cfg.dynamicSmemBytes = KD_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)splits;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    cudaError_t e;
+    switch (splits) {
+        case 1: e = cudaLaunchKernelEx(&cfg, kd_gemm_kernel<1>, mapA, mapX, g); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, kd_gemm_kernel<2>, mapA, mapX, g); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, kd_gemm_kernel<4>, mapA, mapX, g); break;
+        case 8: e = cudaLaunchKernelEx(&cfg, kd_gemm_kernel<8>, mapA, mapX, g); break;
+        default: return OT_ERR_CUDA;
+    }
+    return e == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}
+
+// The GEMM kernels' shared-memory opt-in.
+static bool kd_gemm_attrs() {
+    return cudaFuncSetAttribute(kd_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, KD_SMEM) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kd_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KD_SMEM) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kd_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, KD_SMEM) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kd_gemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, KD_SMEM) ==
+               cudaSuccess;
 }
 
 }  // namespace cyc
@@ -434,14 +570,12 @@ extern "C" int ot_kdomain_solve(int m, const float* G, int ld, float eps, int nr
     float* V = (float*)(w + L.V);
     __nv_bfloat16* Ut = (__nv_bfloat16*)(w + L.Ut);
     __nv_bfloat16* Vt = (__nv_bfloat16*)(w + L.Vt);
-    float* D = (float*)(w + L.D);
     int* flag = (int*)(w + L.flag);
     CUtensorMap mK, mKt, mU, mV;
     if (!make_map(&mK, K, mp, mp, KD_BM) || !make_map(&mKt, Kt, mp, mp, KD_BM) || !make_map(&mU, Ut, KD_BN, mp, KD_BN) ||
         !make_map(&mV, Vt, KD_BN, mp, KD_BN))
         return OT_ERR_CUDA;
-    if (cudaFuncSetAttribute(kd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, KD_SMEM) != cudaSuccess)
-        return OT_ERR_CUDA;
+    if (!kd_gemm_attrs()) return OT_ERR_CUDA;
     if (cudaMemsetAsync(flag, 0, 64, st) != cudaSuccess) return OT_ERR_CUDA;
     if (row_err && cudaMemsetAsync(row_err, 0, sizeof(float) * KD_BN * (size_t)iters, st) != cudaSuccess)
         return OT_ERR_CUDA;
@@ -451,15 +585,16 @@ extern "C" int ot_kdomain_solve(int m, const float* G, int ld, float eps, int nr
     if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     const unsigned long long tmo = 10000000000ull;
     const dim3 sgrid((mp + 255) / 256 < 64 ? (mp + 255) / 256 : 64, KD_BN);
-    const int splits = kd_splits(mp);
+    GemmArgs gu = {}, gv = {};
+    gu.m = gv.m = m;
+    gu.H = alpha, gu.X = U, gu.Xt = Ut;   // U = alpha ./ (K V)
+    gv.H = beta, gv.X = V, gv.Xt = Vt;    // V = beta ./ (K^T U)
     for (int it = 0; it < iters; ++it) {
-        int rc = kd_gemm(mK, mV, mp, D, flag, tmo, st);   // D = K V (in reduction slices)
+        gu.row_err = row_err ? row_err + (size_t)it * KD_BN : nullptr;
+        int rc = kd_gemm(mK, mV, mp, gu, flag, tmo, st, it > 0);
         if (rc != OT_OK) return rc;
-        kd_scale_kernel<<<sgrid, 256, 0, st>>>(D, splits, alpha, U, Ut, m, mp,
-                                               row_err ? row_err + (size_t)it * KD_BN : nullptr);
-        rc = kd_gemm(mKt, mU, mp, D, flag, tmo, st);       // D = K^T U
+        rc = kd_gemm(mKt, mU, mp, gv, flag, tmo, st, true);
         if (rc != OT_OK) return rc;
-        kd_scale_kernel<<<sgrid, 256, 0, st>>>(D, splits, beta, V, Vt, m, mp, nullptr);
     }
     kd_log_kernel<<<dim3(sgrid.x, KD_BN), 256, 0, st>>>(V, m, mp, nrhs, (double)eps, z_out);
     return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
@@ -479,16 +614,6 @@ extern "C" int ot_kdomain_status(const void* workspace, int m, int* status, void
 
 namespace {
 __device__ int g_kd_product_flag;
-
-__global__ void __launch_bounds__(256) kd_sum_slices_kernel(const float* __restrict__ Dp, int splits, int mp,
-                                                            float* __restrict__ Dt) {
-    const int n = blockIdx.y;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += gridDim.x * blockDim.x) {
-        float d = 0.f;
-        for (int s = 0; s < splits; ++s) d += Dp[((size_t)s * KD_BN + n) * mp + i];
-        Dt[(size_t)n * mp + i] = d;
-    }
-}
 }
 
 // Dt[n][i] = sum_k A[i][k] X[n][k] on the tensor cores (the product inside ot_kdomain_solve).
@@ -501,19 +626,14 @@ extern "C" int ot_kdomain_product(int mp, const void* A, const void* X, float* D
     cudaStream_t st = (cudaStream_t)stream;
     CUtensorMap mA, mX;
     if (!make_map(&mA, (void*)A, mp, mp, KD_BM) || !make_map(&mX, (void*)X, KD_BN, mp, KD_BN)) return OT_ERR_CUDA;
-    if (cudaFuncSetAttribute(kd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, KD_SMEM) != cudaSuccess)
-        return OT_ERR_CUDA;
+    if (!kd_gemm_attrs()) return OT_ERR_CUDA;
     int* flag = nullptr;
     if (cudaGetSymbolAddress((void**)&flag, g_kd_product_flag) != cudaSuccess) return OT_ERR_CUDA;
     if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return OT_ERR_CUDA;
-    // the slices go to the workspace's product region, then one pass sums them into Dt
-    const int splits = kd_splits(mp);
-    if (splits <= 0) return OT_ERR_CUDA;
-    float* Dp = (float*)((char*)workspace + L.D);
-    int rc = kd_gemm(mA, mX, mp, Dp, flag, 10000000000ull, st);
+    GemmArgs g = {};
+    g.D = Dt;
+    int rc = kd_gemm(mA, mX, mp, g, flag, 10000000000ull, st);
     if (rc != OT_OK) return rc;
-    kd_sum_slices_kernel<<<dim3((mp + 255) / 256 < 64 ? (mp + 255) / 256 : 64, KD_BN), 256, 0, st>>>(Dp, splits, mp, Dt);
-    if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
