@@ -6,7 +6,9 @@
 // marginals alpha_n, beta_n of unit mass, one iteration is
 //     U = alpha ./ (K V),    V = beta ./ (K^T U)
 // for all 64 histogram pairs n at once, i.e. two [m x m] x [m x 64] products.
-// K and K^T are stored as BF16 (padded to mp, a multiple of 128), the products
+// K and K^T are stored as BF16 (padded to mp, a multiple of 128) in tile-major
+// order, so that each pipeline stage's [128 x 64] tile is 16 KB of contiguous
+// memory (one DRAM stream per stage instead of 128 rows of 128 bytes); the products
 // accumulate in FP32 in tensor memory.  BF16 limits the fixed point's accuracy
 // to about 1e-3; the FP32 log-domain batch solver then polishes each pair from
 // z = eps log V (warm start) to the requested tolerance.
@@ -151,6 +153,7 @@ __device__ __forceinline__ unsigned long long smem_desc_sw128(const void* tile) 
 
 struct GemmArgs {
     int mp;                       // padded size (multiple of 128)
+    int a_tiled;                  // A in tile-major order (kd_tiled) rather than row-major
     int* err;                     // error flag (OT_ERR_TIMEOUT on an expired wait)
     unsigned long long timeout_ns;
     float* D;                     // [64][mp] product output (H == nullptr)
@@ -210,9 +213,14 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
         // launched without the dependent-launch attribute): they are requested before
         // waiting for the previous product, whose scaling update the X tiles read.
         const int pre = min(nkb, KD_STAGES);
+        // the A tile of reduction block kb: tile-major (one 16 KB run) or row-major
+        const int a_col = g.a_tiled ? 0 : -1;
+        const int a_row0 = g.a_tiled ? (int)blockIdx.x * nkb_total * KD_BM : m0;
         for (int i = 0; i < pre; ++i) {
+            const int kb = kb0 + i;
             mbar_arrive_expect_tx(&full[i], KD_STAGE_BYTES);
-            tma_load_2d(base + (size_t)i * KD_STAGE_BYTES, &tmA, (kb0 + i) * KD_BK, m0, &full[i]);
+            tma_load_2d(base + (size_t)i * KD_STAGE_BYTES, &tmA, a_col < 0 ? kb * KD_BK : 0,
+                        a_col < 0 ? a_row0 : a_row0 + kb * KD_BM, &full[i]);
         }
         grid_dep_wait();
         for (int i = 0; i < pre; ++i)
@@ -227,8 +235,8 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
             }
             unsigned char* st = base + (size_t)s * KD_STAGE_BYTES;
             mbar_arrive_expect_tx(&full[s], KD_STAGE_BYTES);
-            const int kc = (kb0 + i) * KD_BK;
-            tma_load_2d(st, &tmA, kc, m0, &full[s]);
+            const int kb = kb0 + i, kc = kb * KD_BK;
+            tma_load_2d(st, &tmA, a_col < 0 ? kc : 0, a_col < 0 ? a_row0 : a_row0 + kb * KD_BM, &full[s]);
             tma_load_2d(st + KD_A_BYTES, &tmX, kc, 0, &full[s]);
         }
         s_issued = i;
@@ -356,7 +364,13 @@ __global__ void __launch_bounds__(128, 1) kd_gemm_kernel(const __grid_constant__
     cluster_sync();   // the peers have read this CTA's slice
 }
 
-// K = exp(-G / eps) (log2 form: 2^(-G kap)), BF16, and its transpose; zero padding.
+// Tile-major offset of element (i, j) of an [mp][mp] operand: [128 x 64] tiles,
+// those of a row block consecutive, rows of 64 within a tile.
+__device__ __forceinline__ size_t kd_tiled(int i, int j, int mp) {
+    return ((size_t)(i >> 7) * (size_t)(mp >> 6) + (size_t)(j >> 6)) * (KD_BM * KD_BK) + (size_t)((i & 127) * KD_BK + (j & 63));
+}
+
+// K = exp(-G / eps) (log2 form: 2^(-G kap)), BF16, and its transpose, both tile-major; zero padding.
 __global__ void __launch_bounds__(256) kd_kmat_kernel(const float* __restrict__ G, int ld, int m, int mp, float kap,
                                                       __nv_bfloat16* __restrict__ K, __nv_bfloat16* __restrict__ Kt) {
     __shared__ __nv_bfloat16 tile[32][33];
@@ -366,11 +380,11 @@ __global__ void __launch_bounds__(256) kd_kmat_kernel(const float* __restrict__ 
         const int i = by + r, j = bx + tx;
         const float v = (i < m && j < m) ? ex2(-G[(size_t)i * ld + j] * kap) : 0.f;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        K[(size_t)i * mp + j] = h;
+        K[kd_tiled(i, j, mp)] = h;
         tile[r][tx] = h;
     }
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) Kt[(size_t)(bx + r) * mp + by + tx] = tile[tx][r];
+    for (int r = ty; r < 32; r += 8) Kt[kd_tiled(bx + r, by + tx, mp)] = tile[tx][r];
 }
 
 // Unit-mass histograms (FP32 [64][mp], zero padding), first scalings V = 1, U = 0.
@@ -572,7 +586,10 @@ extern "C" int ot_kdomain_solve(int m, const float* G, int ld, float eps, int nr
     __nv_bfloat16* Vt = (__nv_bfloat16*)(w + L.Vt);
     int* flag = (int*)(w + L.flag);
     CUtensorMap mK, mKt, mU, mV;
-    if (!make_map(&mK, K, mp, mp, KD_BM) || !make_map(&mKt, Kt, mp, mp, KD_BM) || !make_map(&mU, Ut, KD_BN, mp, KD_BN) ||
+    // K and K^T tile-major: a [mp mp / 64][64] view whose [128 x 64] boxes are whole tiles
+    const int trows = (int)((size_t)mp * mp / KD_BK);
+    if (!make_map(&mK, K, trows, KD_BK, KD_BM) || !make_map(&mKt, Kt, trows, KD_BK, KD_BM) ||
+        !make_map(&mU, Ut, KD_BN, mp, KD_BN) ||
         !make_map(&mV, Vt, KD_BN, mp, KD_BN))
         return OT_ERR_CUDA;
     if (!kd_gemm_attrs()) return OT_ERR_CUDA;
@@ -586,6 +603,7 @@ extern "C" int ot_kdomain_solve(int m, const float* G, int ld, float eps, int nr
     const unsigned long long tmo = 10000000000ull;
     const dim3 sgrid((mp + 255) / 256 < 64 ? (mp + 255) / 256 : 64, KD_BN);
     GemmArgs gu = {}, gv = {};
+    gu.a_tiled = gv.a_tiled = 1;
     gu.m = gv.m = m;
     gu.H = alpha, gu.X = U, gu.Xt = Ut;   // U = alpha ./ (K V)
     gv.H = beta, gv.X = V, gv.Xt = Vt;    // V = beta ./ (K^T U)

@@ -24,29 +24,40 @@
 //           parallel over the block's threads; the most negative one enters
 //           if it is negative, else the next block of rows is priced, and a
 //           full pass without a candidate proves optimality;
+//  tree     besides parent pointers, every node has its position in a preorder
+//           of the tree and its subtree size, so that a subtree is the
+//           contiguous range [pos, pos + size) and "y is an ancestor of x" is
+//           a range test;
 //  pivot    one thread: the entering arc closes a cycle with the tree paths
-//           from its ends up to their common ancestor; the flow on the cycle's
+//           from its ends up to their common ancestor, found by climbing from
+//           one end until the range holds the other; the flow on the cycle's
 //           backward arcs bounds the step, and of the blocking arcs the last
 //           one met when going round the cycle from that ancestor leaves (the
 //           rule that keeps the tree strongly feasible, so degenerate pivots
-//           cannot cycle); the cut-off subtree is re-hung from the entering
-//           arc by reversing the parent pointers on the path between them;
+//           cannot cycle); the cut-off subtree T is re-hung from the entering
+//           arc by reversing the parent pointers on the path between them,
+//           and only the subtree sizes on the cycle change outside T;
 //  duals    every node's potential is the signed sum of arc costs on its path
 //           to the root (pi(x) = c + pi(parent) over an arc x -> parent,
-//           pi(x) = pi(parent) - c over parent -> x): recomputed from the tree
-//           after each pivot by pointer jumping over all nodes in parallel.
-//           A node's jump pointer and partial sum share one 64-bit word, so
-//           every read sees a consistent pair and the jumps need no barrier
-//           between reads and writes (one per pass, about log2 depth passes).
+//           pi(x) = pi(parent) - c over parent -> x).  A pivot changes the
+//           potentials of T only, all by the entering arc's reduced cost (the
+//           potentials are exact integers, so the shift is exact), and moves
+//           T's range next to its new parent: the re-rooted subtree's preorder
+//           is the old range of each node on the reversed path minus that of
+//           the node below it, concatenated from the entering end up.  One
+//           parallel pass over the nodes applies the shift, the new positions
+//           (a binary search on the nested ranges of the reversed path) and
+//           the path's new sizes.
 //
-// One thread block solves one problem and holds its tree in shared memory, 18
-// bytes per node: the potential with the jump pointer (one 64-bit word), the
-// FP64 flow on the node's parent arc, and the parent and the arc's direction
-// in 16 bits (an original arc is fixed by its two ends, and points from the
-// source to the sink; an arc to the root is artificial).  A launch solves
-// `count` problems of one size at once.
-// Every loop has a bound; a tree found inconsistent ends the solve with
-// OT_ERR_NONFINITE instead of looping.
+// One thread block solves one problem and holds its tree in shared memory, 22
+// bytes per node: the potential with the subtree size (one 64-bit word), the
+// FP64 flow on the node's parent arc, the parent and the arc's direction in 16
+// bits (an original arc is fixed by its two ends, and points from the source
+// to the sink; an arc to the root is artificial), the preorder position, and
+// one slot of the pivot's path buffer.  A launch solves `count` problems of one
+// size at once.  Every loop has a bound; a tree found inconsistent (also by a
+// check of every potential against its parent arc after the last pivot) ends
+// the solve with OT_ERR_NONFINITE instead of looping.
 #include <math.h>
 #include <string.h>
 
@@ -59,7 +70,7 @@ namespace cyc {
 #define LOT_MAXM 5120
 #define LOT_PRICE_ARCS 16384                                 // arcs priced per step (whole rows)
 #define LOT_PPT (LOT_PRICE_ARCS / LOT_BT)                    // arcs per thread and step
-#define LOT_MAX_ROUNDS 20                                    // pointer-jumping rounds (2^20 > any depth)
+#define LOT_NPT ((2 * LOT_MAXM + 1 + LOT_BT - 1) / LOT_BT)   // tree nodes per thread, at most
 
 struct LotArgs {
     int count, m, N;
@@ -125,58 +136,61 @@ __device__ __forceinline__ double lot_sum(double x, double* s_v) {
     return t;
 }
 
-// A node's word: jump pointer in the top 14 bits, potential (|pi| < 2^46) as a
-// 50-bit two's-complement field below it.
-#define LOT_PB 50
-#define LOT_MARK 0x3fff   // jump-pointer value marking a node during a pivot (above any node index)
-
-__device__ __forceinline__ long long lot_pack(int anc, long long pi) {
-    return (long long)(((unsigned long long)anc << LOT_PB) | ((unsigned long long)pi & ((1ull << LOT_PB) - 1)));
-}
-__device__ __forceinline__ int lot_anc(long long w) { return (int)((unsigned long long)w >> LOT_PB); }
-__device__ __forceinline__ long long lot_pi(long long w) { return (long long)((unsigned long long)w << (64 - LOT_PB)) >> (64 - LOT_PB); }
+// A node's word: pi 2^14 + size, the potential (|pi| < 2^46) above the subtree
+// size (1 <= size <= 2m + 1 < 2^14).  Adding d 2^14 shifts the potential, adding
+// d the size.
+#define LOT_SB 14
+__device__ __forceinline__ long long lot_pack(long long pi, int size) { return pi * (1ll << LOT_SB) + size; }
+__device__ __forceinline__ long long lot_pi(long long w) { return w >> LOT_SB; }
+__device__ __forceinline__ int lot_size(long long w) { return (int)(w & ((1ll << LOT_SB) - 1)); }
 
 // Original arc between node x and its parent y (one a source, the other a sink).
 __device__ __forceinline__ int lot_arc(int x, int y, int m) {
     return x < m ? x * m + (y - m) : y * m + (x - m);
 }
 
-// One pivot (a single thread).  pu[x] = 2 parent + up (up = 1 when x's parent
-// arc points from x to the parent; the root is its own parent), flow[x] the
-// flow on that arc; the jump-pointer fields of the words serve as marks here
-// (every one is the root when a pivot starts).  Returns 0 or an OT_ERR_*.
-__device__ int lot_pivot(int e, int m, unsigned short* pu, long long* word, double* flow) {
-    const int V = 2 * m + 1, R = 2 * m;
+// What the parallel pass of a pivot needs: T = the old range [a0, a0 + s), its
+// new parent at old position P, the reversed path chain[0..k) (chain[0] the
+// entering end, chain[k - 1] the node whose parent arc left) and the shift.
+struct LotMove {
+    int a0, s, P, k;
+    long long sigma;
+};
+
+// The serial part of one pivot (a single thread) on the entering arc e with
+// reduced cost rc < 0.  pu[x] = 2 parent + up (up = 1 when x's parent arc points
+// from x to the parent; the root is its own parent), flow[x] the flow on that
+// arc, pos and the size field of word the preorder ranges.  Updates the flows,
+// the parent pointers of the reversed path and the sizes on the cycle outside
+// T; T's potentials, positions and sizes are left to the parallel pass.
+// Returns 0 or an OT_ERR_*.
+__device__ int lot_pivot(int e, long long rc, int m, unsigned short* pu, unsigned short* pos, long long* word,
+                         double* flow, unsigned short* chain, LotMove* mv) {
+    const int V = 2 * m + 1;
     const int u = e / m, v = m + (e - (e / m) * m);
-    // common ancestor w: mark the path from u to the root, climb from v to a mark
-    int x = u;
-    for (int s = 0;; ++s) {
-        if (s > V) return OT_ERR_NONFINITE;
-        word[x] = lot_pack(LOT_MARK, lot_pi(word[x]));
-        if (x == R) break;
-        x = pu[x] >> 1;
-    }
-    int w = v;
-    for (int s = 0; lot_anc(word[w]) != LOT_MARK; ++s) {
-        if (s > V) return OT_ERR_NONFINITE;
-        w = pu[w] >> 1;
-    }
     // leaving arc: the cycle runs w -> ... -> u (down), u -> v, v -> ... -> w (up).
     // Backward arcs: on the u side those pointing up, on the v side those pointing
     // down.  Of the blocking arcs the last in that order leaves: on the u side the
     // deepest (strict <, climbing from u), on the v side the highest (<=, climbing
-    // from v, and after every u-side arc).
+    // from v, and after every u-side arc).  The climb from u ends at the common
+    // ancestor w, the first node whose range holds v.
+    const int pv = pos[v];
     double delta = INFINITY;
     int leave = -1, leave_u = 0;
     int len = 0;
-    for (x = u; x != w; x = pu[x] >> 1) {
+    int x = u;
+    for (;;) {
+        const int px = pos[x];
+        if (px <= pv && pv < px + lot_size(word[x])) break;
         if (++len > V) return OT_ERR_NONFINITE;
         if ((pu[x] & 1) && flow[x] < delta) {
             delta = flow[x];
             leave = x;
             leave_u = 1;
         }
+        x = pu[x] >> 1;
     }
+    const int w = x;
     for (x = v; x != w; x = pu[x] >> 1) {
         if (++len > V) return OT_ERR_NONFINITE;
         if (!(pu[x] & 1) && flow[x] <= delta) {
@@ -186,19 +200,30 @@ __device__ int lot_pivot(int e, int m, unsigned short* pu, long long* word, doub
         }
     }
     if (leave < 0 || !(delta < INFINITY)) return OT_ERR_NONFINITE;   // cannot happen: every cycle has a backward arc
-    for (x = u; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? -delta : delta;
-    for (x = v; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? delta : -delta;
-    // re-hang: q is the entering arc's end inside the cut-off subtree; the path
-    // q -> ... -> leave is reversed, each node taking over its old child's arc
-    // (the reversed path holds original arcs only: an artificial arc joins a node
-    // to the root, which stays above the leaving arc)
+    if (delta > 0.0) {
+        for (x = u; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? -delta : delta;
+        for (x = v; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? delta : -delta;
+    }
+    // re-hang: q is the entering arc's end inside T; the path q -> ... -> leave is
+    // reversed, each node taking over its old child's arc (the reversed path holds
+    // original arcs only: an artificial arc joins a node to the root, which stays
+    // above the leaving arc)
     const int q = leave_u ? u : v;
-    int np = leave_u ? v : u;
+    const int nparent = leave_u ? v : u;
+    const int s = lot_size(word[leave]);
+    const int l0 = pu[leave] >> 1;   // leave's old parent, on the cycle
+    mv->a0 = pos[leave];
+    mv->s = s;
+    mv->P = pos[nparent];
+    mv->sigma = leave_u ? rc : -rc;   // the entering arc's reduced cost becomes 0
+    int np = nparent;
     int nup = leave_u ? 1 : 0;   // u -> v points up from u, down to v
     double nfl = delta;
+    int k = 0;
     x = q;
-    for (int s = 0;; ++s) {
-        if (s > V) return OT_ERR_NONFINITE;
+    for (;;) {
+        if (k >= V) return OT_ERR_NONFINITE;
+        chain[k++] = (unsigned short)x;
         const int op = pu[x] >> 1, oup = pu[x] & 1;
         const double ofl = flow[x];
         pu[x] = (unsigned short)(2 * np + nup);
@@ -209,19 +234,68 @@ __device__ int lot_pivot(int e, int m, unsigned short* pu, long long* word, doub
         nfl = ofl;
         x = op;
     }
+    mv->k = k;
+    // sizes outside T: leave's old ancestors below w lose T, the new parent's gain it
+    len = 0;
+    for (x = l0; x != w; x = pu[x] >> 1) {
+        if (++len > V) return OT_ERR_NONFINITE;
+        word[x] -= s;
+    }
+    for (x = nparent; x != w; x = pu[x] >> 1) {
+        if (++len > V) return OT_ERR_NONFINITE;
+        word[x] += s;
+    }
     return OT_OK;
+}
+
+// Node x after the move mv, packed in 32 bits: the new position (bits 0-13), x in
+// T (bit 14: its potential shifts by mv.sigma), x on the reversed path (bit 15)
+// with its new subtree size (bits 16-29).  Reads old positions and the sizes of
+// the path's nodes, which the pass writes only after a barrier.
+__device__ __forceinline__ unsigned lot_move_node(int x, const LotMove& mv, const unsigned short* pos,
+                                                  const long long* word, const unsigned short* chain) {
+    const int xp = pos[x];
+    if (xp >= mv.a0 && xp < mv.a0 + mv.s) {
+        // the first path node whose range holds xp (the ranges grow along the path)
+        int lo = 0, hi = mv.k - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int c = chain[mid], cp = pos[c];
+            if (cp <= xp && xp < cp + lot_size(word[c]))
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const int c = chain[lo], cp = pos[c];
+        int off, psz = 0;
+        if (lo == 0) {
+            off = xp - cp;
+        } else {
+            const int pc = chain[lo - 1], pp = pos[pc];
+            psz = lot_size(word[pc]);
+            off = psz + xp - cp - (xp >= pp + psz ? psz : 0);
+        }
+        const unsigned np = (unsigned)((mv.P < mv.a0 ? mv.P + 1 : mv.P + 1 - mv.s) + off);
+        if (x != c) return np | 0x4000u;
+        return np | 0xC000u | ((unsigned)(lo == 0 ? mv.s : mv.s - psz) << 16);   // a reversed path's new size
+    }
+    if (mv.P < mv.a0) return (unsigned)((xp > mv.P && xp < mv.a0) ? xp + mv.s : xp);
+    return (unsigned)((xp >= mv.a0 + mv.s && xp <= mv.P) ? xp - mv.s : xp);
 }
 
 __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_constant__ LotArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
     const int m = A.m, V = 2 * m + 1, R = 2 * m;
-    long long* word = reinterpret_cast<long long*>(dsm);                  // [V] jump pointer + potential
+    long long* word = reinterpret_cast<long long*>(dsm);                  // [V] potential + subtree size
     double* flow = reinterpret_cast<double*>(word + V);                   // [V] flow on the parent arc
     unsigned short* pu = reinterpret_cast<unsigned short*>(flow + V);     // [V] 2 parent + up
+    unsigned short* pos = pu + V;                                         // [V] preorder position
+    unsigned short* chain = pos + V;                                      // [V] a pivot's reversed path
     __shared__ double s_v[LOT_BW + 1];
     __shared__ long long s_q[LOT_BW + 1];
     __shared__ int s_i[LOT_BW + 1];
     __shared__ int s_err;
+    __shared__ LotMove s_mv;
 
     const int p = blockIdx.x, tid = threadIdx.x;
     const long long mm = (long long)m * m;
@@ -277,22 +351,26 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     const float sc = ldexpf(1.0f, k2);
     const long long M = ((long long)ldexpf(gmax, k2) + 1) * (long long)V;
 
-    // ---- strongly feasible artificial start
+    // ---- strongly feasible artificial start: the root (position 0) and every other
+    // node as a leaf below it, at position x + 1
     for (int x = tid; x < V; x += LOT_BT) {
         if (x == R) {
             pu[x] = (unsigned short)(2 * R);
             flow[x] = 0.0;
-            word[x] = lot_pack(R, 0);
+            word[x] = lot_pack(0, V);
+            pos[x] = 0;
         } else if (x < m) {
             const double al = (double)a[x] * ia;
             const int up = al > 0.0 ? 1 : 0;   // a zero supply hangs below the root with zero flow
             pu[x] = (unsigned short)(2 * R + up);
             flow[x] = al;
-            word[x] = lot_pack(R, up ? M : -M);
+            word[x] = lot_pack(up ? M : -M, 1);
+            pos[x] = (unsigned short)(x + 1);
         } else {
             pu[x] = (unsigned short)(2 * R);   // root -> sink
             flow[x] = (double)b[x - m] * ib;
-            word[x] = lot_pack(R, -M);
+            word[x] = lot_pack(-M, 1);
+            pos[x] = (unsigned short)(x + 1);
         }
     }
     if (tid == 0) s_err = 0;
@@ -300,7 +378,6 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     // ---- pivots
     const int rb = max(1, min(m, LOT_PRICE_ARCS / m));   // rows per pricing step (rb m <= LOT_PRICE_ARCS)
     const int qstep = LOT_BT / m, rstep = LOT_BT - (LOT_BT / m) * m;
-    const int npt = (V + LOT_BT - 1) / LOT_BT;            // tree nodes per thread
     long long piv = 0;
     int status = OT_OK;
     int cursor = 0, scanned = 0;
@@ -344,57 +421,53 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             status = OT_ERR_NOT_CONVERGED;
             break;
         }
-        if (tid == 0) s_err = lot_pivot(be, m, pu, word, flow);
+        if (tid == 0) s_err = lot_pivot(be, best, m, pu, pos, word, flow, chain, &s_mv);
         __syncthreads();
         if (s_err != OT_OK) {
             status = s_err;
             break;
         }
         ++piv;
-        // potentials by pointer jumping: word[x] = (anc, pi(x) - pi(anc)) until anc is the root
-        for (int k = 0; k < npt; ++k) {
-            const int x = tid + k * LOT_BT;
-            if (x < V) {
-                if (x == R) {
-                    word[x] = lot_pack(R, 0);
-                } else {
-                    const int y = pu[x] >> 1;
-                    const long long c = y == R ? M : (long long)__float2int_rn(G[lot_arc(x, y, m)] * sc);
-                    word[x] = lot_pack(y, (pu[x] & 1) ? c : -c);
-                }
-            }
-        }
-        __syncthreads();
-        // passes: each owned node jumps to its pointer's pointer and adds its partial sum.
-        // Only a node's owner writes its word, and every word (one 64-bit shared-memory
-        // access) satisfies the invariant, so reads racing with writes are harmless; a
-        // jump pointer only moves up, and a pass that finds every pointer at the root ends
-        int rounds = 0;
+        // T's potentials, every moved position and the reversed path's sizes: all
+        // reads, a barrier, then all writes
         {
-            volatile long long* vw = word;
-            for (;;) {
-                int any = 0;
-                for (int k = 0; k < npt; ++k) {
-                    const int x = tid + k * LOT_BT;
-                    if (x >= V) break;
-                    const long long w = vw[x];
-                    const int y = lot_anc(w);
-                    if (y != R) {
-                        const long long w2 = vw[y];
-                        vw[x] = lot_pack(lot_anc(w2), lot_pi(w) + lot_pi(w2));
-                        any = 1;
+            const LotMove mv = s_mv;
+            unsigned nx[LOT_NPT];
+#pragma unroll
+            for (int k = 0; k < LOT_NPT; ++k) {
+                const int x = tid + k * LOT_BT;
+                if (x < V) nx[k] = lot_move_node(x, mv, pos, word, chain);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < LOT_NPT; ++k) {
+                const int x = tid + k * LOT_BT;
+                if (x < V) {
+                    pos[x] = (unsigned short)(nx[k] & 0x3fffu);
+                    if (nx[k] & 0x4000u) {
+                        long long w = word[x] + mv.sigma * (1ll << LOT_SB);
+                        if (nx[k] & 0x8000u) w += (long long)(nx[k] >> 16) - lot_size(w);
+                        word[x] = w;
                     }
                 }
-                if (!__syncthreads_or(any)) break;
-                if (++rounds > LOT_MAX_ROUNDS) break;   // uniform; caught below
             }
-        }
-        if (rounds > LOT_MAX_ROUNDS) {
-            status = OT_ERR_NONFINITE;
-            break;
         }
     }
     __syncthreads();
+    // every potential against its parent arc: a wrong incremental update shows here
+    {
+        int bad_tree = 0;
+        for (int x = tid; x < V; x += LOT_BT) {
+            if (x == R) {
+                bad_tree |= lot_pi(word[x]) != 0;
+                continue;
+            }
+            const int y = pu[x] >> 1;
+            const long long c = y == R ? M : (long long)__float2int_rn(G[lot_arc(x, y, m)] * sc);
+            bad_tree |= lot_pi(word[x]) != lot_pi(word[y]) + ((pu[x] & 1) ? c : -c);
+        }
+        if (__syncthreads_or(bad_tree) && status == OT_OK) status = OT_ERR_NONFINITE;
+    }
 
     // ---- outputs: the plan from the basic flows, duals u_i = pi(i) - pi(0), v_j = pi(0) - pi(m + j)
     for (long long e = tid; e < mm; e += LOT_BT) S[e] = 0.f;
@@ -453,9 +526,9 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     }
 }
 
-size_t lot_smem_bytes(int m) { return (size_t)18 * (2 * (size_t)m + 1) + 16; }
+size_t lot_smem_bytes(int m) { return (size_t)22 * (2 * (size_t)m + 1) + 16; }
 static_assert(2 * (2 * LOT_MAXM + 1) < 0xffff, "parent and direction fit 16 bits");
-static_assert(2 * LOT_MAXM < LOT_MARK, "node indices fit the 14-bit jump pointer, below the mark");
+static_assert(2 * LOT_MAXM + 1 < (1 << LOT_SB), "subtree sizes fit their 14-bit field");
 
 }  // namespace cyc
 
