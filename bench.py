@@ -732,6 +732,8 @@ def run_ours_precision(args, rank, world, local_rank):
         "speedup_bf16_vs_fp32": t32 / t16,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": (peak_src + " (MEASURED_PEAKS.json hbm_gbs)") if peak_src == "measured"
+                     else peak_src + " (6.8 TB/s)",
                      "kernel": f"kd_gemm_kernel pair per BF16 iteration at mp = {mp} (K and K^T read once)",
                      "tensor_tflops": tflops,
                      "tensor_frac_of_bf16_peak": tflops / peaks.get("bf16_tflops", 1900.0),

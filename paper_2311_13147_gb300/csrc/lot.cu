@@ -71,6 +71,7 @@ namespace cyc {
 #define LOT_PRICE_ARCS 16384                                 // arcs priced per step (whole rows)
 #define LOT_PPT (LOT_PRICE_ARCS / LOT_BT)                    // arcs per thread and step
 #define LOT_NPT ((2 * LOT_MAXM + 1 + LOT_BT - 1) / LOT_BT)   // tree nodes per thread, at most
+#define LOT_CPK 256                                          // reversed-path ranges kept packed for the move pass
 
 struct LotArgs {
     int count, m, N;
@@ -104,8 +105,8 @@ __device__ __forceinline__ void lot_argmin(long long& v, int& idx, long long* s_
     }
     __syncthreads();
     if (w == 0) {
-        v = s_v[lane];
-        idx = s_i[lane];
+        v = lane < LOT_BW ? s_v[lane] : 0x7fffffffffffffffll;
+        idx = lane < LOT_BW ? s_i[lane] : 0x7fffffff;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -150,100 +151,157 @@ __device__ __forceinline__ int lot_arc(int x, int y, int m) {
 }
 
 // What the parallel pass of a pivot needs: T = the old range [a0, a0 + s), its
-// new parent at old position P, the reversed path chain[0..k) (chain[0] the
-// entering end, chain[k - 1] the node whose parent arc left) and the shift.
+// new parent at old position P, the reversed path p_0..p_{k-1} (p_0 the entering
+// end, p_{k-1} the node whose parent arc left; p_t = chain[t] when dir = 1,
+// chain[V - 1 - t] when dir = -1) and the potential shift.
 struct LotMove {
-    int a0, s, P, k;
+    int a0, s, P, k, dir;
     long long sigma;
 };
 
-// The serial part of one pivot (a single thread) on the entering arc e with
-// reduced cost rc < 0.  pu[x] = 2 parent + up (up = 1 when x's parent arc points
-// from x to the parent; the root is its own parent), flow[x] the flow on that
-// arc, pos and the size field of word the preorder ranges.  Updates the flows,
-// the parent pointers of the reversed path and the sizes on the cycle outside
-// T; T's potentials, positions and sizes are left to the parallel pass.
-// Returns 0 or an OT_ERR_*.
-__device__ int lot_pivot(int e, long long rc, int m, unsigned short* pu, unsigned short* pos, long long* word,
-                         double* flow, unsigned short* chain, LotMove* mv) {
-    const int V = 2 * m + 1;
+__device__ __forceinline__ int lot_path_at(const unsigned short* chain, int V, int dir, int t) {
+    return dir > 0 ? chain[t] : chain[V - 1 - t];
+}
+
+// Warp minimum of (flow, rank) pairs: the smaller flow, then the smaller rank.
+__device__ __forceinline__ void lot_warp_argmin(double& f, int& r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double of = __shfl_xor_sync(0xffffffffu, f, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+        if (of < f || (of == f && orr < r)) {
+            f = of;
+            r = orr;
+        }
+    }
+}
+
+// One pivot by the 32 lanes of one warp, on the entering arc e with reduced cost
+// rc < 0.  pu[x] = 2 parent + up (up = 1 when x's parent arc points from x to the
+// parent; the root is its own parent), flow[x] the flow on that arc, pos and the
+// size field of word the preorder ranges.  Updates the flows, the parent
+// pointers of the reversed path and the sizes on the cycle outside T; T's
+// potentials, positions and sizes are left to the block's parallel pass.
+// Returns 0 or an OT_ERR_* (the same value in every lane).
+//
+//  1. lane 0 climbs from u, lane 1 from v, each until the node's range holds the
+//     other end (both stop at the common ancestor w), recording the nodes below
+//     w: the u side from chain[0] up, the v side from chain[V - 1] down;
+//  2. the cycle runs w -> ... -> u (down), u -> v, v -> ... -> w (up); its
+//     backward arcs are those pointing up on the u side and down on the v side,
+//     and of the blocking ones the last met in that order leaves: ranked, the v
+//     side's from the highest down come first, then the u side's from the
+//     deepest up, and the warp takes the smallest (flow, rank);
+//  3. the step moves along both sides in parallel;
+//  4. the path from the entering end q to the leaving node is reversed, each node
+//     taking over its old child's arc (all of a lane group's reads before its
+//     writes, groups from the leaving end down, so no old value is overwritten
+//     before it is read); the reversed path holds original arcs only, since an
+//     artificial arc joins a node to the root, which stays above the leaving arc;
+//  5. the leaving node's old ancestors below w lose T's size, the new parent's
+//     gain it.
+__device__ int lot_pivot_warp(int e, long long rc, int m, unsigned short* pu, unsigned short* pos, long long* word,
+                              double* flow, unsigned short* chain, unsigned* cpk, LotMove* mv) {
+    const int V = 2 * m + 1, lane = threadIdx.x & 31;
     const int u = e / m, v = m + (e - (e / m) * m);
-    // leaving arc: the cycle runs w -> ... -> u (down), u -> v, v -> ... -> w (up).
-    // Backward arcs: on the u side those pointing up, on the v side those pointing
-    // down.  Of the blocking arcs the last in that order leaves: on the u side the
-    // deepest (strict <, climbing from u), on the v side the highest (<=, climbing
-    // from v, and after every u-side arc).  The climb from u ends at the common
-    // ancestor w, the first node whose range holds v.
-    const int pv = pos[v];
-    double delta = INFINITY;
-    int leave = -1, leave_u = 0;
+    // 1. the two climbs
     int len = 0;
-    int x = u;
-    for (;;) {
-        const int px = pos[x];
-        if (px <= pv && pv < px + lot_size(word[x])) break;
-        if (++len > V) return OT_ERR_NONFINITE;
-        if ((pu[x] & 1) && flow[x] < delta) {
-            delta = flow[x];
-            leave = x;
-            leave_u = 1;
-        }
-        x = pu[x] >> 1;
-    }
-    const int w = x;
-    for (x = v; x != w; x = pu[x] >> 1) {
-        if (++len > V) return OT_ERR_NONFINITE;
-        if (!(pu[x] & 1) && flow[x] <= delta) {
-            delta = flow[x];
-            leave = x;
-            leave_u = 0;
+    if (lane < 2) {
+        int x = lane == 0 ? u : v;
+        const int po = pos[lane == 0 ? v : u];
+        for (;;) {
+            const int px = pos[x], sx = lot_size(word[x]), nx = pu[x] >> 1;   // one round trip per step
+            if (px <= po && po < px + sx) break;
+            if (len >= V) {
+                len = V + 1;   // inconsistent tree
+                break;
+            }
+            chain[lane == 0 ? len : V - 1 - len] = (unsigned short)x;
+            ++len;
+            x = nx;
         }
     }
-    if (leave < 0 || !(delta < INFINITY)) return OT_ERR_NONFINITE;   // cannot happen: every cycle has a backward arc
+    const int ku = __shfl_sync(0xffffffffu, len, 0), kv = __shfl_sync(0xffffffffu, len, 1);
+    if (ku + kv > V - 1) return OT_ERR_NONFINITE;
+    __syncwarp();
+    // 2. the leaving arc
+    double f = INFINITY;
+    int r = 0x7fffffff;
+    for (int t = lane; t < ku + kv; t += 32) {
+        const bool vside = t < kv;
+        const int x = vside ? chain[V - 1 - t] : chain[t - kv];
+        const int up = pu[x] & 1;
+        if (vside ? !up : up) {
+            const double fx = flow[x];
+            const int rx = vside ? kv - 1 - t : t;   // v side: highest first; then u side: deepest first
+            if (fx < f || (fx == f && rx < r)) {
+                f = fx;
+                r = rx;
+            }
+        }
+    }
+    lot_warp_argmin(f, r);
+    if (r == 0x7fffffff || !(f < INFINITY)) return OT_ERR_NONFINITE;   // cannot happen: every cycle has a backward arc
+    const double delta = f;
+    const int leave_u = r >= kv;
+    const int li = leave_u ? r - kv : kv - 1 - r;   // the leaving node's index along its side
+    const int leave = leave_u ? chain[li] : chain[V - 1 - li];
+    // 3. the step
     if (delta > 0.0) {
-        for (x = u; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? -delta : delta;
-        for (x = v; x != w; x = pu[x] >> 1) flow[x] += (pu[x] & 1) ? delta : -delta;
+        for (int t = lane; t < ku + kv; t += 32) {
+            const bool vside = t < kv;
+            const int x = vside ? chain[V - 1 - t] : chain[t - kv];
+            const bool upx = pu[x] & 1;
+            flow[x] += (vside ? upx : !upx) ? delta : -delta;
+        }
     }
-    // re-hang: q is the entering arc's end inside T; the path q -> ... -> leave is
-    // reversed, each node taking over its old child's arc (the reversed path holds
-    // original arcs only: an artificial arc joins a node to the root, which stays
-    // above the leaving arc)
-    const int q = leave_u ? u : v;
+    __syncwarp();
+    // 4. re-hang along p_0 = q .. p_li = leave
+    const int dir = leave_u ? 1 : -1;
     const int nparent = leave_u ? v : u;
     const int s = lot_size(word[leave]);
-    const int l0 = pu[leave] >> 1;   // leave's old parent, on the cycle
-    mv->a0 = pos[leave];
-    mv->s = s;
-    mv->P = pos[nparent];
-    mv->sigma = leave_u ? rc : -rc;   // the entering arc's reduced cost becomes 0
-    int np = nparent;
-    int nup = leave_u ? 1 : 0;   // u -> v points up from u, down to v
-    double nfl = delta;
-    int k = 0;
-    x = q;
-    for (;;) {
-        if (k >= V) return OT_ERR_NONFINITE;
-        chain[k++] = (unsigned short)x;
-        const int op = pu[x] >> 1, oup = pu[x] & 1;
-        const double ofl = flow[x];
-        pu[x] = (unsigned short)(2 * np + nup);
-        flow[x] = nfl;
-        if (x == leave) break;
-        np = x;
-        nup = oup ^ 1;   // the same arc seen from the other end
-        nfl = ofl;
-        x = op;
+    for (int t0 = (li / 32) * 32; t0 >= 0; t0 -= 32) {
+        const int t = t0 + lane;
+        int npu = 0;
+        double nfl = 0.0;
+        if (t <= li) {
+            if (t == 0) {
+                npu = 2 * nparent + (leave_u ? 1 : 0);   // u -> v points up from u, down to v
+                nfl = delta;
+            } else {
+                const int c = lot_path_at(chain, V, dir, t - 1);   // the old child on the path
+                npu = 2 * c + ((pu[c] & 1) ^ 1);                   // the same arc seen from the other end
+                nfl = flow[c];
+            }
+        }
+        __syncwarp();
+        if (t <= li) {
+            const int x = lot_path_at(chain, V, dir, t);
+            pu[x] = (unsigned short)npu;
+            flow[x] = nfl;
+            // the path's (unchanged) range, packed for the move pass's binary search
+            if (t < LOT_CPK) cpk[t] = (unsigned)pos[x] | ((unsigned)lot_size(word[x]) << 16);
+        }
+        __syncwarp();
     }
-    mv->k = k;
-    // sizes outside T: leave's old ancestors below w lose T, the new parent's gain it
-    len = 0;
-    for (x = l0; x != w; x = pu[x] >> 1) {
-        if (++len > V) return OT_ERR_NONFINITE;
-        word[x] -= s;
+    // 5. sizes on the cycle outside T
+    for (int t = lane; t < ku + kv; t += 32) {
+        const bool vside = t < kv;
+        const int i = vside ? t : t - kv;    // index along its side
+        const int x = vside ? chain[V - 1 - t] : chain[t - kv];
+        if (vside == (bool)leave_u) {
+            word[x] += s;                    // the new parent's side, up to w
+        } else if (i > li) {
+            word[x] -= s;                    // above the leaving node on its side
+        }
     }
-    for (x = nparent; x != w; x = pu[x] >> 1) {
-        if (++len > V) return OT_ERR_NONFINITE;
-        word[x] += s;
+    if (lane == 0) {
+        mv->a0 = pos[leave];
+        mv->s = s;
+        mv->P = pos[nparent];
+        mv->k = li + 1;
+        mv->dir = dir;
+        mv->sigma = leave_u ? rc : -rc;   // the entering arc's reduced cost becomes 0
     }
     return OT_OK;
 }
@@ -252,31 +310,48 @@ __device__ int lot_pivot(int e, long long rc, int m, unsigned short* pu, unsigne
 // T (bit 14: its potential shifts by mv.sigma), x on the reversed path (bit 15)
 // with its new subtree size (bits 16-29).  Reads old positions and the sizes of
 // the path's nodes, which the pass writes only after a barrier.
-__device__ __forceinline__ unsigned lot_move_node(int x, const LotMove& mv, const unsigned short* pos,
-                                                  const long long* word, const unsigned short* chain) {
+// The old range of the reversed path's node t: packed when t < LOT_CPK, else from the tree.
+__device__ __forceinline__ void lot_path_range(int t, int V, const LotMove& mv, const unsigned short* pos,
+                                               const long long* word, const unsigned short* chain,
+                                               const unsigned* cpk, int& p, int& sz) {
+    if (t < LOT_CPK) {
+        const unsigned v = cpk[t];
+        p = (int)(v & 0xffffu);
+        sz = (int)(v >> 16);
+    } else {
+        const int c = lot_path_at(chain, V, mv.dir, t);
+        p = pos[c];
+        sz = lot_size(word[c]);
+    }
+}
+
+__device__ __forceinline__ unsigned lot_move_node(int x, int V, const LotMove& mv, const unsigned short* pos,
+                                                  const long long* word, const unsigned short* chain,
+                                                  const unsigned* cpk) {
     const int xp = pos[x];
     if (xp >= mv.a0 && xp < mv.a0 + mv.s) {
         // the first path node whose range holds xp (the ranges grow along the path)
         int lo = 0, hi = mv.k - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            const int c = chain[mid], cp = pos[c];
-            if (cp <= xp && xp < cp + lot_size(word[c]))
+            int cp, cs;
+            lot_path_range(mid, V, mv, pos, word, chain, cpk, cp, cs);
+            if (cp <= xp && xp < cp + cs)
                 hi = mid;
             else
                 lo = mid + 1;
         }
-        const int c = chain[lo], cp = pos[c];
-        int off, psz = 0;
+        int cp, cs, off, psz = 0;
+        lot_path_range(lo, V, mv, pos, word, chain, cpk, cp, cs);
         if (lo == 0) {
             off = xp - cp;
         } else {
-            const int pc = chain[lo - 1], pp = pos[pc];
-            psz = lot_size(word[pc]);
+            int pp;
+            lot_path_range(lo - 1, V, mv, pos, word, chain, cpk, pp, psz);
             off = psz + xp - cp - (xp >= pp + psz ? psz : 0);
         }
         const unsigned np = (unsigned)((mv.P < mv.a0 ? mv.P + 1 : mv.P + 1 - mv.s) + off);
-        if (x != c) return np | 0x4000u;
+        if (xp != cp) return np | 0x4000u;   // positions are unique: xp == cp exactly for the path node
         return np | 0xC000u | ((unsigned)(lo == 0 ? mv.s : mv.s - psz) << 16);   // a reversed path's new size
     }
     if (mv.P < mv.a0) return (unsigned)((xp > mv.P && xp < mv.a0) ? xp + mv.s : xp);
@@ -296,6 +371,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     __shared__ int s_i[LOT_BW + 1];
     __shared__ int s_err;
     __shared__ LotMove s_mv;
+    __shared__ unsigned s_cpk[LOT_CPK];
 
     const int p = blockIdx.x, tid = threadIdx.x;
     const long long mm = (long long)m * m;
@@ -378,6 +454,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     // ---- pivots
     const int rb = max(1, min(m, LOT_PRICE_ARCS / m));   // rows per pricing step (rb m <= LOT_PRICE_ARCS)
     const int qstep = LOT_BT / m, rstep = LOT_BT - (LOT_BT / m) * m;
+    const bool vec4 = (m & 3) == 0 && ((uintptr_t)A.G & 15) == 0;   // rows of whole, aligned float4s
     long long piv = 0;
     int status = OT_OK;
     int cursor = 0, scanned = 0;
@@ -386,7 +463,30 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         const int r1 = min(m, cursor + rb);
         long long best = 0x7fffffffffffffffll;
         int be = 0x7fffffff;
-        {
+        if (vec4) {
+            // m % 4 == 0: four consecutive arcs of one row per load, e = cursor m + 4 (tid + k LOT_BT)
+            const int e_end = r1 * m;
+            const float4* G4 = reinterpret_cast<const float4*>(G);
+#pragma unroll
+            for (int k = 0; k < LOT_PPT / 4; ++k) {
+                const int e = cursor * m + 4 * (tid + k * LOT_BT);
+                if (e < e_end) {
+                    const float4 c4 = G4[e >> 2];
+                    const int r = e / m, j = e - r * m;
+                    const long long pr = lot_pi(word[r]);
+                    const longlong2 w01 = *reinterpret_cast<const longlong2*>(word + m + j);
+                    const longlong2 w23 = *reinterpret_cast<const longlong2*>(word + m + j + 2);
+                    const long long r0 = (long long)__float2int_rn(c4.x * sc) - pr + lot_pi(w01.x);
+                    const long long r1v = (long long)__float2int_rn(c4.y * sc) - pr + lot_pi(w01.y);
+                    const long long r2 = (long long)__float2int_rn(c4.z * sc) - pr + lot_pi(w23.x);
+                    const long long r3 = (long long)__float2int_rn(c4.w * sc) - pr + lot_pi(w23.y);
+                    if (r0 < best) { best = r0; be = e; }
+                    if (r1v < best) { best = r1v; be = e + 1; }
+                    if (r2 < best) { best = r2; be = e + 2; }
+                    if (r3 < best) { best = r3; be = e + 3; }
+                }
+            }
+        } else {
             // arcs e = cursor m + tid + k LOT_BT of rows [cursor, r1): all loads issued up front
             const int e_end = r1 * m;
             int e = cursor * m + tid;
@@ -421,7 +521,10 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             status = OT_ERR_NOT_CONVERGED;
             break;
         }
-        if (tid == 0) s_err = lot_pivot(be, best, m, pu, pos, word, flow, chain, &s_mv);
+        if (tid < 32) {
+            const int st = lot_pivot_warp(be, best, m, pu, pos, word, flow, chain, s_cpk, &s_mv);
+            if (tid == 0) s_err = st;
+        }
         __syncthreads();
         if (s_err != OT_OK) {
             status = s_err;
@@ -436,7 +539,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
 #pragma unroll
             for (int k = 0; k < LOT_NPT; ++k) {
                 const int x = tid + k * LOT_BT;
-                if (x < V) nx[k] = lot_move_node(x, mv, pos, word, chain);
+                if (x < V) nx[k] = lot_move_node(x, V, mv, pos, word, chain, s_cpk);
             }
             __syncthreads();
 #pragma unroll
