@@ -731,7 +731,10 @@ def run_ours_precision(args, rank, world, local_rank):
         "bf16_then_polish": {"ms_per_step": t16, "polish_iters_per_cost": it16},
         "speedup_bf16_vs_fp32": t32 / t16,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "frac": gbs / peaks["hbm_gbs"],
+                     # DRAM bytes of the pair of products of one iteration (ncu, the same mp)
+                     "traffic": (2 * kd_traffic) if (kd_traffic := profile_traffic(
+                         "kd_gemm_kernel.kdomain_m8192.md", "kgemm.cu")) and mp == 8192 else None,
                      "peak_source": (peak_src + " (MEASURED_PEAKS.json hbm_gbs)") if peak_src == "measured"
                      else peak_src + " (6.8 TB/s)",
                      "kernel": f"kd_gemm_kernel pair per BF16 iteration at mp = {mp} (K and K^T read once)",

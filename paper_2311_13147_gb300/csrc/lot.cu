@@ -20,19 +20,22 @@
 //           sink, over artificial arcs of cost M = (max|g| + 1)(2m + 1), a
 //           strongly feasible spanning tree (a zero-flow arc points away from
 //           the root);
-//  pricing  reduced costs g_ij - pi(i) + pi(m + j) of a block of rows, in
-//           parallel over the block's threads; the most negative one enters
+//  pricing  reduced costs g_ij - pi(i) + pi(m + j) of a block of rows (about
+//           16384 arcs), in parallel over the block's threads, four arcs per
+//           16-byte load when m is a multiple of 4; the most negative one enters
 //           if it is negative, else the next block of rows is priced, and a
 //           full pass without a candidate proves optimality;
 //  tree     besides parent pointers, every node has its position in a preorder
 //           of the tree and its subtree size, so that a subtree is the
 //           contiguous range [pos, pos + size) and "y is an ancestor of x" is
 //           a range test;
-//  pivot    one thread: the entering arc closes a cycle with the tree paths
+//  pivot    one warp: the entering arc closes a cycle with the tree paths
 //           from its ends up to their common ancestor, found by climbing from
-//           one end until the range holds the other; the flow on the cycle's
-//           backward arcs bounds the step, and of the blocking arcs the last
-//           one met when going round the cycle from that ancestor leaves (the
+//           each end (two lanes at once) until the range holds the other end;
+//           the paths are recorded, and the rest of the pivot runs over them
+//           in parallel.  The flow on the cycle's backward arcs bounds the
+//           step, and of the blocking arcs the last one met when going round
+//           the cycle from that ancestor leaves (the
 //           rule that keeps the tree strongly feasible, so degenerate pivots
 //           cannot cycle); the cut-off subtree T is re-hung from the entering
 //           arc by reversing the parent pointers on the path between them,
@@ -156,6 +159,7 @@ __device__ __forceinline__ int lot_arc(int x, int y, int m) {
 // chain[V - 1 - t] when dir = -1) and the potential shift.
 struct LotMove {
     int a0, s, P, k, dir;
+    int lbase, lcap;   // free part of the path buffer, [lbase, lbase + lcap): T's node list
     long long sigma;
 };
 
@@ -301,6 +305,8 @@ __device__ int lot_pivot_warp(int e, long long rc, int m, unsigned short* pu, un
         mv->P = pos[nparent];
         mv->k = li + 1;
         mv->dir = dir;
+        mv->lbase = ku;
+        mv->lcap = V - ku - kv;
         mv->sigma = leave_u ? rc : -rc;   // the entering arc's reduced cost becomes 0
     }
     return OT_OK;
@@ -372,6 +378,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     __shared__ int s_err;
     __shared__ LotMove s_mv;
     __shared__ unsigned s_cpk[LOT_CPK];
+    __shared__ int s_cnt;
 
     const int p = blockIdx.x, tid = threadIdx.x;
     const long long mm = (long long)m * m;
@@ -521,9 +528,18 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             status = OT_ERR_NOT_CONVERGED;
             break;
         }
+        {
+            // the next pricing block's costs into L2 while the pivot runs
+            const size_t b0 = (size_t)cursor * m * 4, b1 = (size_t)min(m, cursor + rb) * m * 4;
+            for (size_t off = b0 + (size_t)tid * 128; off < b1; off += (size_t)LOT_BT * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)G + off));
+        }
         if (tid < 32) {
             const int st = lot_pivot_warp(be, best, m, pu, pos, word, flow, chain, s_cpk, &s_mv);
-            if (tid == 0) s_err = st;
+            if (tid == 0) {
+                s_err = st;
+                s_cnt = 0;
+            }
         }
         __syncthreads();
         if (s_err != OT_OK) {
@@ -531,10 +547,45 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             break;
         }
         ++piv;
-        // T's potentials, every moved position and the reversed path's sizes: all
-        // reads, a barrier, then all writes
-        {
-            const LotMove mv = s_mv;
+        // T's potentials, every moved position and the reversed path's sizes
+        const LotMove mv = s_mv;
+        if (mv.k <= LOT_CPK && mv.s <= mv.lcap) {
+            // the path's ranges are all packed, so no node's update reads another's:
+            // nodes between T and its new place move at once; T's nodes are listed in
+            // the free part of the path buffer (one append per warp), then updated
+            unsigned short* list = chain + mv.lbase;
+            for (int k = 0; k < LOT_NPT; ++k) {
+                const int x = tid + k * LOT_BT;
+                const int xp = x < V ? pos[x] : -1;
+                const bool inT = xp >= mv.a0 && xp < mv.a0 + mv.s;
+                if (x < V && !inT) {
+                    if (mv.P < mv.a0) {
+                        if (xp > mv.P && xp < mv.a0) pos[x] = (unsigned short)(xp + mv.s);
+                    } else if (xp >= mv.a0 + mv.s && xp <= mv.P) {
+                        pos[x] = (unsigned short)(xp - mv.s);
+                    }
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, inT);
+                if (ball) {
+                    int base = 0;
+                    if ((tid & 31) == 0) base = atomicAdd(&s_cnt, __popc(ball));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const int slot = base + __popc(ball & ((1u << (tid & 31)) - 1u));
+                    if (inT && slot < mv.lcap) list[slot] = (unsigned short)x;   // s slots fit; a corrupt tree cannot overflow
+                }
+            }
+            __syncthreads();
+            const int nT = min(s_cnt, mv.lcap);   // == mv.s in a consistent tree
+            for (int i = tid; i < nT; i += LOT_BT) {
+                const int x = list[i];
+                const unsigned r = lot_move_node(x, V, mv, pos, word, chain, s_cpk);
+                pos[x] = (unsigned short)(r & 0x3fffu);
+                long long w = word[x] + mv.sigma * (1ll << LOT_SB);
+                if (r & 0x8000u) w += (long long)(r >> 16) - lot_size(w);
+                word[x] = w;
+            }
+        } else {
+            // all reads, a barrier, then all writes
             unsigned nx[LOT_NPT];
 #pragma unroll
             for (int k = 0; k < LOT_NPT; ++k) {
