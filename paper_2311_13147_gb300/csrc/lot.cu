@@ -72,7 +72,13 @@ namespace cyc {
 #define LOT_BW (LOT_BT / 32)
 #define LOT_MAXM 5120
 #define LOT_PRICE_ARCS 16384                                 // arcs priced per step (whole rows)
-#define LOT_PPT (LOT_PRICE_ARCS / LOT_BT)                    // arcs per thread and step
+#define LOT_PPT (LOT_PRICE_ARCS / LOT_BT)                    // arcs per thread and pass
+
+// Passes of LOT_PRICE_ARCS arcs per pricing step: a wider block finds better entering
+// arcs (fewer pivots: on the paper's synthetic costs 68072 -> 33011 at m = 5000 with
+// four passes) but costs more per scan, which pays only when the pivots are dear.
+__device__ __forceinline__ int lot_price_passes(int m) { return m >= 4000 ? 4 : m >= 1500 ? 2 : 1; }
+
 #define LOT_NPT ((2 * LOT_MAXM + 1 + LOT_BT - 1) / LOT_BT)   // tree nodes per thread, at most
 #define LOT_CPK 256                                          // reversed-path ranges kept packed for the move pass
 
@@ -151,6 +157,34 @@ __device__ __forceinline__ int lot_size(long long w) { return (int)(w & ((1ll <<
 // Original arc between node x and its parent y (one a source, the other a sink).
 __device__ __forceinline__ int lot_arc(int x, int y, int m) {
     return x < m ? x * m + (y - m) : y * m + (x - m);
+}
+
+// Reduced costs of the arcs [e0, e0 + NP LOT_PRICE_ARCS) below e_end, four consecutive
+// arcs of one row per 16-byte load (m % 4 == 0, 16-byte aligned costs); the most
+// negative one (the first on ties) is merged into (best, be).
+template <int NP>
+__device__ __forceinline__ void lot_price_vec4(const float* G, const long long* word, int m, int e0, int e_end,
+                                               float sc, long long& best, int& be) {
+    const float4* G4 = reinterpret_cast<const float4*>(G);
+#pragma unroll
+    for (int k = 0; k < NP * LOT_PPT / 4; ++k) {
+        const int e = e0 + 4 * ((int)threadIdx.x + k * LOT_BT);
+        if (e < e_end) {
+            const float4 c4 = G4[e >> 2];
+            const int r = e / m, j = e - r * m;
+            const long long pr = lot_pi(word[r]);
+            const longlong2 w01 = *reinterpret_cast<const longlong2*>(word + m + j);
+            const longlong2 w23 = *reinterpret_cast<const longlong2*>(word + m + j + 2);
+            const long long r0 = (long long)__float2int_rn(c4.x * sc) - pr + lot_pi(w01.x);
+            const long long r1 = (long long)__float2int_rn(c4.y * sc) - pr + lot_pi(w01.y);
+            const long long r2 = (long long)__float2int_rn(c4.z * sc) - pr + lot_pi(w23.x);
+            const long long r3 = (long long)__float2int_rn(c4.w * sc) - pr + lot_pi(w23.y);
+            if (r0 < best) { best = r0; be = e; }
+            if (r1 < best) { best = r1; be = e + 1; }
+            if (r2 < best) { best = r2; be = e + 2; }
+            if (r3 < best) { best = r3; be = e + 3; }
+        }
+    }
 }
 
 // What the parallel pass of a pivot needs: T = the old range [a0, a0 + s), its
@@ -459,7 +493,8 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     if (tid == 0) s_err = 0;
 
     // ---- pivots
-    const int rb = max(1, min(m, LOT_PRICE_ARCS / m));   // rows per pricing step (rb m <= LOT_PRICE_ARCS)
+    const int npass = lot_price_passes(m);
+    const int rb = max(1, min(m, npass * LOT_PRICE_ARCS / m));   // rows per pricing step (rb m <= npass LOT_PRICE_ARCS)
     const int qstep = LOT_BT / m, rstep = LOT_BT - (LOT_BT / m) * m;
     const bool vec4 = (m & 3) == 0 && ((uintptr_t)A.G & 15) == 0;   // rows of whole, aligned float4s
     long long piv = 0;
@@ -470,49 +505,37 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         const int r1 = min(m, cursor + rb);
         long long best = 0x7fffffffffffffffll;
         int be = 0x7fffffff;
+        const int e_end = r1 * m;
         if (vec4) {
-            // m % 4 == 0: four consecutive arcs of one row per load, e = cursor m + 4 (tid + k LOT_BT)
-            const int e_end = r1 * m;
-            const float4* G4 = reinterpret_cast<const float4*>(G);
-#pragma unroll
-            for (int k = 0; k < LOT_PPT / 4; ++k) {
-                const int e = cursor * m + 4 * (tid + k * LOT_BT);
-                if (e < e_end) {
-                    const float4 c4 = G4[e >> 2];
-                    const int r = e / m, j = e - r * m;
-                    const long long pr = lot_pi(word[r]);
-                    const longlong2 w01 = *reinterpret_cast<const longlong2*>(word + m + j);
-                    const longlong2 w23 = *reinterpret_cast<const longlong2*>(word + m + j + 2);
-                    const long long r0 = (long long)__float2int_rn(c4.x * sc) - pr + lot_pi(w01.x);
-                    const long long r1v = (long long)__float2int_rn(c4.y * sc) - pr + lot_pi(w01.y);
-                    const long long r2 = (long long)__float2int_rn(c4.z * sc) - pr + lot_pi(w23.x);
-                    const long long r3 = (long long)__float2int_rn(c4.w * sc) - pr + lot_pi(w23.y);
-                    if (r0 < best) { best = r0; be = e; }
-                    if (r1v < best) { best = r1v; be = e + 1; }
-                    if (r2 < best) { best = r2; be = e + 2; }
-                    if (r3 < best) { best = r3; be = e + 3; }
-                }
-            }
+            // all NP passes' loads in one unrolled sequence (independent, so all in flight)
+            if (npass == 4)
+                lot_price_vec4<4>(G, word, m, cursor * m, e_end, sc, best, be);
+            else if (npass == 2)
+                lot_price_vec4<2>(G, word, m, cursor * m, e_end, sc, best, be);
+            else
+                lot_price_vec4<1>(G, word, m, cursor * m, e_end, sc, best, be);
         } else {
-            // arcs e = cursor m + tid + k LOT_BT of rows [cursor, r1): all loads issued up front
-            const int e_end = r1 * m;
-            int e = cursor * m + tid;
-            int r = e / m, j = e - r * m;
+            for (int ps = 0; ps < npass; ++ps) {
+                // arcs e = cursor m + ps LOT_PRICE_ARCS + tid + k LOT_BT below e_end: a pass's loads issued up front
+                int e = cursor * m + ps * LOT_PRICE_ARCS + tid;
+                int r = e / m, j = e - r * m;
 #pragma unroll
-            for (int k = 0; k < LOT_PPT; ++k) {
-                if (e < e_end) {
-                    const long long rc = (long long)__float2int_rn(G[e] * sc) - lot_pi(word[r]) + lot_pi(word[m + j]);
-                    if (rc < best) {
-                        best = rc;
-                        be = e;
+                for (int k = 0; k < LOT_PPT; ++k) {
+                    if (e < e_end) {
+                        const long long rc =
+                            (long long)__float2int_rn(G[e] * sc) - lot_pi(word[r]) + lot_pi(word[m + j]);
+                        if (rc < best) {
+                            best = rc;
+                            be = e;
+                        }
                     }
-                }
-                e += LOT_BT;
-                j += rstep;
-                r += qstep;
-                if (j >= m) {
-                    j -= m;
-                    ++r;
+                    e += LOT_BT;
+                    j += rstep;
+                    r += qstep;
+                    if (j >= m) {
+                        j -= m;
+                        ++r;
+                    }
                 }
             }
         }

@@ -174,9 +174,12 @@ def test_single_point_closed_form(cy):
     assert r["value"] == pytest.approx(2.5, rel=1e-12)
 
 
-@pytest.mark.parametrize("m,N", [(1024, 10), (5120, 2)])
+@pytest.mark.parametrize("m,N", [(1024, 10), (1502, 3), (2500, 2), (5120, 2)])
 def test_certificate_at_large_sizes(cy, m, N):
-    """Up to the largest supported block (m = 5120; the paper's d = 10000, N = 2 has m = 5000)."""
+    """Up to the largest supported block (m = 5120; the paper's d = 10000, N = 2 has m = 5000).
+
+    The sizes cover each pricing width (one, two and four passes of 16384 arcs) and, at
+    m = 1502 (not a multiple of 4), the scalar pricing path over two passes."""
     p = I.paper_synthetic_problem(m, N, seed=7)
     S, u, v, r, G = solve(cy, p)
     assert r["status"] == cy.OT_OK
