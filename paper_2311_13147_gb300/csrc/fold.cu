@@ -141,11 +141,47 @@ __global__ void __launch_bounds__(OT_BLOCK) fold_points(int m, int N, const floa
     }
 }
 
+// Two FP32 lanes per instruction (f32x2 arithmetic, the same rounding as two scalar operations).
+typedef unsigned long long fx2;
+__device__ __forceinline__ fx2 fx_pk(float a, float b) {
+    fx2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 fx_up(fx2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ fx2 fx_sub(fx2 a, fx2 b) {
+    fx2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ fx2 fx_mul(fx2 a, fx2 b) {
+    fx2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ fx2 fx_fma(fx2 a, fx2 b, fx2 c) {
+    fx2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ fx2 fx_add(fx2 a, fx2 b) {
+    fx2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Points, column strips: a block takes 256 consecutive columns (one per thread) and a
 // run of rows.  Each thread rotates its target point once per item (NK registers
 // pairs), then per row forms the N costs, their minimum and, for the soft-min, the
 // sum of exp2((min - C_k) kappa) in a second pass over registers (no branch).
 // Stores are coalesced (a row of 256 consecutive entries per block).  N <= NK.
+// The soft-min works on pairs of blocks (f32x2): the rotated targets of blocks
+// k >= N sit at 1e30, so their costs are +inf, they never win the minimum and
+// their exponentials are 0.
 template <int MODE, int NK>
 __global__ void __launch_bounds__(OT_BLOCK) fold_points_strip(int m, int N, const float2* __restrict__ x,
                                                               const float2* __restrict__ y, float kappa,
@@ -175,6 +211,40 @@ __global__ void __launch_bounds__(OT_BLOCK) fold_points_strip(int m, int N, cons
             yy[k] = r.y * yj.x + r.x * yj.y;
         }
         const int i0 = rc * rows_per_item, i1 = min(m, i0 + rows_per_item);
+        if constexpr (MODE == OT_SOFTMIN) {
+            fx2 YX[NK / 2], YY[NK / 2];
+#pragma unroll
+            for (int q = 0; q < NK / 2; ++q) {
+                YX[q] = fx_pk(2 * q < N ? yx[2 * q] : 1e30f, 2 * q + 1 < N ? yx[2 * q + 1] : 1e30f);
+                YY[q] = fx_pk(2 * q < N ? yy[2 * q] : 1e30f, 2 * q + 1 < N ? yy[2 * q + 1] : 1e30f);
+            }
+            const fx2 nk = fx_pk(-kappa, -kappa);
+#pragma unroll 2
+            for (int i = i0; i < i1; ++i) {
+                const float2 xi = __ldg(x + i);
+                const fx2 X = fx_pk(xi.x, xi.x), Y = fx_pk(xi.y, xi.y);
+                fx2 c[NK / 2];
+                float mn = INFINITY;
+#pragma unroll
+                for (int q = 0; q < NK / 2; ++q) {
+                    const fx2 dx = fx_sub(X, YX[q]), dy = fx_sub(Y, YY[q]);
+                    c[q] = fx_fma(dx, dx, fx_mul(dy, dy));
+                    const float2 cv = fx_up(c[q]);
+                    mn = fminf(mn, fminf(cv.x, cv.y));
+                }
+                const float mk = mn * kappa;
+                const fx2 mk2 = fx_pk(mk, mk);
+                fx2 s2 = fx_pk(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < NK / 2; ++q) {
+                    const float2 a = fx_up(fx_fma(c[q], nk, mk2));
+                    s2 = fx_add(s2, fx_pk(ex2(a.x), ex2(a.y)));
+                }
+                const float2 sv = fx_up(s2);
+                G[(long long)i * m + j] = fmaf(-inv, lg2(sv.x + sv.y), mn);
+            }
+            continue;
+        }
 #pragma unroll 2
         for (int i = i0; i < i1; ++i) {
             const float2 xi = __ldg(x + i);

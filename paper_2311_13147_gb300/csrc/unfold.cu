@@ -100,31 +100,66 @@ __global__ void __launch_bounds__(OT_BLOCK) unfold_kernel(int m, int N, const fl
 }
 
 // EROT unfold, 4 consecutive columns per thread (m % 4 == 0, 16-byte aligned
-// buffers).  An item is one block k, a strip of 1024 columns and a run of rows:
-// the strip's column potentials are split into (hi, lo) once per item (the FP64
-// work of this GPU is slow), then sub-tiles of UT_R rows are formed with the
-// tile's cost rows (or points) loaded before any exponential, stores with the
-// streaming hint.
+// buffers).  An item is one block k, a strip of 1024 columns and a run of at most
+// UT_RMAX rows: the strip's column potentials and the run's row potentials are
+// split into (hi, lo) once per item (the FP64 work of this GPU is slow; one
+// barrier per item), then sub-tiles of UT_R rows are formed with the tile's cost
+// rows (or points) loaded before any exponential, two entries per f32x2
+// instruction, stores with the streaming hint.
 #define UT_C4 (4 * OT_BLOCK)
+#define UT_RMAX 1024
+typedef unsigned long long ux2;
+__device__ __forceinline__ ux2 ux_pk(float a, float b) {
+    ux2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 ux_up(ux2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ ux2 ux_add(ux2 a, ux2 b) {
+    ux2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ ux2 ux_sub(ux2 a, ux2 b) {
+    ux2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ ux2 ux_mul(ux2 a, ux2 b) {
+    ux2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ ux2 ux_fma(ux2 a, ux2 b, ux2 c) {
+    ux2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 template <bool POINTS>
 __global__ void __launch_bounds__(OT_BLOCK) unfold_erot_vec4(int m, int N, const double* __restrict__ w,
                                                              const double* __restrict__ z,
                                                              const float* __restrict__ C, const float2* __restrict__ x,
                                                              const float2* __restrict__ y, float kappa, int dense,
                                                              int rows_per_item, float* __restrict__ T) {
-    __shared__ float s_wh[UT_R], s_wl[UT_R];
+    __shared__ float2 s_w[UT_RMAX];   // the run's row potentials (hi, lo)
     __shared__ float4 s_zh[OT_BLOCK], s_zl[OT_BLOCK];
     __shared__ float2 s_rot;
     const int strips = (m + UT_C4 - 1) / UT_C4, chunks = (m + rows_per_item - 1) / rows_per_item;
     const long long nitems = (long long)N * strips * chunks;
     const long long n = (long long)N * m;
     const int m4 = m >> 2;
+    const ux2 nk = ux_pk(-kappa, -kappa);
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int k = (int)(item / ((long long)strips * chunks));
         const int rem = (int)(item - (long long)k * strips * chunks);
         const int r_beg = (rem / strips) * rows_per_item, g0 = (rem % strips) * OT_BLOCK;   // float4 column index
         const int r_end = min(m, r_beg + rows_per_item);
-        __syncthreads();
+        __syncthreads();   // the previous item's potentials are no longer read
         {
             const int g = g0 + threadIdx.x;
             float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
@@ -135,6 +170,11 @@ __global__ void __launch_bounds__(OT_BLOCK) unfold_erot_vec4(int m, int N, const
             s_zh[threadIdx.x] = make_float4(h[0], h[1], h[2], h[3]);
             s_zl[threadIdx.x] = make_float4(l[0], l[1], l[2], l[3]);
         }
+        for (int t = threadIdx.x; t < r_end - r_beg; t += OT_BLOCK) {
+            float hi, lo;
+            split_f64(w[r_beg + t] * (double)kappa, hi, lo);
+            s_w[t] = make_float2(hi, lo);
+        }
         if (POINTS && threadIdx.x == 0) {
             float sn, cs;
             sincospif(2.0f * (float)k / (float)N, &sn, &cs);
@@ -142,44 +182,41 @@ __global__ void __launch_bounds__(OT_BLOCK) unfold_erot_vec4(int m, int N, const
         }
         __syncthreads();
         const int g = g0 + threadIdx.x;
-        const bool gv = g < m4;
+        if (g >= m4) continue;
         const float4 zh = s_zh[threadIdx.x], zl = s_zl[threadIdx.x];
-        float2 yk[4];
+        const ux2 ZH01 = ux_pk(zh.x, zh.y), ZH23 = ux_pk(zh.z, zh.w), ZL01 = ux_pk(zl.x, zl.y), ZL23 = ux_pk(zl.z, zl.w);
+        ux2 YX01 = 0, YX23 = 0, YY01 = 0, YY23 = 0;
         if (POINTS) {
+            float2 yk[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float2 yj = gv ? y[4 * g + c] : make_float2(0.f, 0.f);
+                const float2 yj = y[4 * g + c];
                 yk[c] = make_float2(s_rot.x * yj.x - s_rot.y * yj.y, s_rot.y * yj.x + s_rot.x * yj.y);
             }
+            YX01 = ux_pk(yk[0].x, yk[1].x);
+            YX23 = ux_pk(yk[2].x, yk[3].x);
+            YY01 = ux_pk(yk[0].y, yk[1].y);
+            YY23 = ux_pk(yk[2].y, yk[3].y);
         }
         for (int i0 = r_beg; i0 < r_end; i0 += UT_R) {
-            __syncthreads();   // the previous sub-tile's row potentials are no longer read
-            if (threadIdx.x < UT_R) {
-                const int i = i0 + threadIdx.x;
-                float hi = 0.f, lo = 0.f;
-                if (i < r_end) split_f64(w[i] * (double)kappa, hi, lo);
-                s_wh[threadIdx.x] = hi;
-                s_wl[threadIdx.x] = lo;
-            }
-            __syncthreads();
-            if (!gv) continue;
             const int nr = min(UT_R, r_end - i0);
-            float4 cst[UT_R];
+            ux2 c01[UT_R], c23[UT_R];
 #pragma unroll
             for (int r = 0; r < UT_R; ++r) {
                 if (r < nr) {
                     const int i = i0 + r;
                     if (POINTS) {
                         const float2 xi = x[i];
-                        float cc[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float dx = xi.x - yk[c].x, dy = xi.y - yk[c].y;
-                            cc[c] = fmaf(dx, dx, dy * dy);
-                        }
-                        cst[r] = make_float4(cc[0], cc[1], cc[2], cc[3]);
+                        const ux2 X = ux_pk(xi.x, xi.x), Y = ux_pk(xi.y, xi.y);
+                        ux2 dx = ux_sub(X, YX01), dy = ux_sub(Y, YY01);
+                        c01[r] = ux_fma(dx, dx, ux_mul(dy, dy));
+                        dx = ux_sub(X, YX23);
+                        dy = ux_sub(Y, YY23);
+                        c23[r] = ux_fma(dx, dx, ux_mul(dy, dy));
                     } else {
-                        cst[r] = __ldg(reinterpret_cast<const float4*>(C + (long long)k * m * m + (long long)i * m) + g);
+                        const float4 cv = __ldg(reinterpret_cast<const float4*>(C + (long long)k * m * m + (long long)i * m) + g);
+                        c01[r] = ux_pk(cv.x, cv.y);
+                        c23[r] = ux_pk(cv.z, cv.w);
                     }
                 }
             }
@@ -187,12 +224,12 @@ __global__ void __launch_bounds__(OT_BLOCK) unfold_erot_vec4(int m, int N, const
             for (int r = 0; r < UT_R; ++r) {
                 if (r < nr) {
                     const int i = i0 + r;
-                    const float wh = s_wh[r], wl = s_wl[r];
-                    float4 v;
-                    v.x = ex2(fmaf(cst[r].x, -kappa, wh + zh.x) + (wl + zl.x));
-                    v.y = ex2(fmaf(cst[r].y, -kappa, wh + zh.y) + (wl + zl.y));
-                    v.z = ex2(fmaf(cst[r].z, -kappa, wh + zh.z) + (wl + zl.z));
-                    v.w = ex2(fmaf(cst[r].w, -kappa, wh + zh.w) + (wl + zl.w));
+                    const float2 wv = s_w[i - r_beg];
+                    const ux2 WH = ux_pk(wv.x, wv.x), WL = ux_pk(wv.y, wv.y);
+                    // 2^(hi + lo - kappa c): the same operations, in the same order, as one lane at a time
+                    const float2 a01 = ux_up(ux_add(ux_fma(c01[r], nk, ux_add(WH, ZH01)), ux_add(WL, ZL01)));
+                    const float2 a23 = ux_up(ux_add(ux_fma(c23[r], nk, ux_add(WH, ZH23)), ux_add(WL, ZL23)));
+                    const float4 v = make_float4(ex2(a01.x), ex2(a01.y), ex2(a23.x), ex2(a23.y));
                     if (!dense) {
                         __stcs(reinterpret_cast<float4*>(T + (long long)k * m * m + (long long)i * m) + g, v);
                     } else {
@@ -239,6 +276,7 @@ extern "C" int ot_unfold_plan(int mode, int m, int N, const void* S_or_w, const 
         long long rpi = ((long long)N * strips * m + 8LL * sms - 1) / (8LL * sms);
         rpi = (rpi + UT_R - 1) / UT_R * UT_R;
         if (rpi < UT_R) rpi = UT_R;
+        if (rpi > UT_RMAX) rpi = UT_RMAX;   // the run's row potentials fit the block's table
         const long long nt4 = (long long)N * strips * ((m + rpi - 1) / rpi);
         const int g4 = (int)(nt4 < (long long)sms * 8 ? nt4 : (long long)sms * 8);
         if (C_base)

@@ -90,8 +90,9 @@ def test_fold_softmin_stored(cy, m, N, seed):
     assert err <= 4e-7 * np.abs(Go).max() + 1e-6 * p.eps, err
 
 
-@pytest.mark.parametrize("m,N,seed", [(60, 4, 0), (33, 8, 1), (1024, 8, 2)])
+@pytest.mark.parametrize("m,N,seed", [(60, 4, 0), (33, 8, 1), (1024, 8, 2), (100, 3, 3), (300, 16, 4), (150, 11, 5)])
 def test_fold_from_points(cy, m, N, seed):
+    """Column-strip folds for N <= 16 (4, 8 or 16 blocks per pass; N = 3 and 11 pad the last pair)."""
     p = I.sector_problem(m, N, seed=seed, eps_frac=0.05)
     x = dev(p.x.astype(np.float32))
     for mode in (cy.OT_SOFTMIN, cy.OT_MIN):
@@ -227,8 +228,9 @@ def test_unfold_lot_bit_exact(cy):
     assert np.array_equal(host(Td), OR.assemble_block_circulant(To.astype(np.float64)).astype(np.float32))
 
 
-@pytest.mark.parametrize("m,N,seed", [(60, 4, 0), (37, 3, 1), (300, 5, 2)])
+@pytest.mark.parametrize("m,N,seed", [(60, 4, 0), (37, 3, 1), (300, 5, 2), (1024, 4, 3)])
 def test_unfold_erot(cy, m, N, seed):
+    """Compact, dense and from-points unfolds; m = 1024 gives each item a run of many sub-tiles."""
     p = I.sector_problem(m, N, seed=seed, eps_frac=0.02)
     Cb, G, w, z, res = _solve_reduced(cy, p, 1e-6)
     wg, zg = host(w), host(z)
