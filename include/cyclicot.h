@@ -455,13 +455,18 @@ size_t ot_lot_workspace_bytes(int count, int m);
  * pricing, the strongly-feasible-tree leaving rule).  Its value times N is the
  * value of the full C-LOT (Theorem 1 with mass 1/N blocks; the N block rows of
  * the full plan are alike); ot_unfold_plan(OT_PLAN_LOT) turns S into the
- * full plan (Eq. optimal_solution_problem_CLOT).  One thread block per
- * problem; `count` problems of the same m in one launch.
+ * full plan (Eq. optimal_solution_problem_CLOT).  One thread block, or one
+ * cluster of them, per problem; `count` problems of the same m in one launch.
  *  G: [count][m][m] FP32 device, finite (ot_fold_cost(OT_MIN) output).
  *  a_base, b_base: [count][m] FP32 device, >= 0 with positive sums; normalised
  *     internally so that alpha, beta have mass 1/N.
- *  opt: max_iter is the pivot cap per problem (>= 1); the other fields are
- *     not used.
+ *  opt: max_iter is the pivot cap per problem (>= 1); timeout_ns bounds each
+ *     wait between the CTAs that share one problem (0 = 10 s; an expired wait
+ *     ends that problem with OT_ERR_TIMEOUT); debug_flags bit 2
+ *     (OT_DEBUG_NO_CLUSTER) keeps one thread block per problem.  When the
+ *     launch fits, each problem gets a thread-block cluster of 2, 4 or 8 CTAs
+ *     that price separate parts of a wider block of arcs (one owns the tree);
+ *     the other fields are not used.
  *  S: [count][m][m] FP32 device output, the optimal basic plan (at most 2m - 1
  *     nonzeros per problem; the flows are kept in FP64 while pivoting).
  *  u, v: [count][m] FP64 device outputs, optimal duals: u_i + v_j <= G_ij,

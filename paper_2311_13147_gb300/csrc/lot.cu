@@ -52,13 +52,13 @@
 //           (a binary search on the nested ranges of the reversed path) and
 //           the path's new sizes.
 //
-// One thread block solves one problem and holds its tree in shared memory, 22
-// bytes per node: the potential with the subtree size (one 64-bit word), the
-// FP64 flow on the node's parent arc, the parent and the arc's direction in 16
-// bits (an original arc is fixed by its two ends, and points from the source
-// to the sink; an arc to the root is artificial), the preorder position, and
-// one slot of the pivot's path buffer.  A launch solves `count` problems of one
-// size at once.  Every loop has a bound; a tree found inconsistent (also by a
+// One thread block (CTA 0 of a cluster, when several price) solves one problem
+// and holds its tree in shared memory, 22 bytes per node: the potential with
+// the subtree size (one 64-bit word), the FP64 flow on the node's parent arc,
+// the parent and the arc's direction in 16 bits (an original arc is fixed by
+// its two ends, and points from the source to the sink; an arc to the root is
+// artificial), the preorder position, and one slot of the pivot's path buffer.
+// A launch solves `count` problems of one size at once.  Every loop has a bound; a tree found inconsistent (also by a
 // check of every potential against its parent arc after the last pivot) ends
 // the solve with OT_ERR_NONFINITE instead of looping.
 #include <math.h>
@@ -93,7 +93,64 @@ struct LotArgs {
     double* v;
     ot_result* res;        // [count]
     double* sums;          // [count][2m] row and column sums of the returned plan (workspace)
+    unsigned long long timeout_ns;   // bound on each wait between the CTAs of a cluster
 };
+
+// ---- thread-block cluster helpers (one instance per cluster of CL CTAs)
+__device__ __forceinline__ unsigned lot_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Address of this variable in CTA `rank` of the cluster (the shared layout is the same in every CTA).
+__device__ __forceinline__ unsigned lot_mapa(const void* p, unsigned rank) {
+    unsigned a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_addr(p)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ void lot_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void lot_remote_arrive(unsigned addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ long long lot_ld_remote64(unsigned addr) {
+    long long v;
+    asm volatile("ld.shared::cluster.b64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ int lot_ld_remote32(unsigned addr) {
+    int v;
+    asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned short lot_ld_remote16(unsigned addr) {
+    unsigned short v;
+    asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void lot_st_remote64(unsigned addr, long long v) {
+    asm volatile("st.shared::cluster.b64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void lot_st_remote32(unsigned addr, int v) {
+    asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// Bounded wait for phase `parity` of a barrier that other CTAs of the cluster arrive on.
+__device__ __forceinline__ bool lot_wait_cluster(unsigned long long* bar, unsigned parity, unsigned long long timeout_ns) {
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (globaltimer() - t0 > timeout_ns) return false;
+    }
+}
 
 // Block minimum of (value, index) pairs; ties go to the smaller index.  Every
 // thread returns the result.
@@ -398,6 +455,15 @@ __device__ __forceinline__ unsigned lot_move_node(int x, int V, const LotMove& m
     return (unsigned)((xp >= mv.a0 + mv.s && xp <= mv.P) ? xp - mv.s : xp);
 }
 
+// CL > 1: one instance per cluster of CL CTAs.  CTA 0 (the owner) holds the tree and
+// pivots; every CTA keeps a copy of the potentials and prices its own part of a
+// pricing block CL times as wide (one pass each), and the owner takes the most
+// negative reduced cost over the parts (the smallest arc on ties, so the choice is
+// the single-CTA one over the wide block).  Per round the other CTAs hand their
+// candidates to the owner and the owner hands back its decision through mbarriers
+// with bounded waits; after a pivot they shift their copies over the re-hung
+// subtree's node list (or copy all potentials when the move took the full pass).
+template <int CL>
 __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_constant__ LotArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
     const int m = A.m, V = 2 * m + 1, R = 2 * m;
@@ -413,8 +479,17 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     __shared__ LotMove s_mv;
     __shared__ unsigned s_cpk[LOT_CPK];
     __shared__ int s_cnt;
+    // cluster hand-offs (CL > 1)
+    __shared__ __align__(8) unsigned long long mb_cand, mb_go;
+    __shared__ long long s_cv[CL > 1 ? CL : 1];
+    __shared__ int s_ce[CL > 1 ? CL : 1];
+    __shared__ long long s_best;
+    __shared__ int s_be, s_dec, s_flag;
+    __shared__ float s_gmax;
+    __shared__ int s_bad;
 
-    const int p = blockIdx.x, tid = threadIdx.x;
+    const int rank = CL > 1 ? (int)lot_rank() : 0;
+    const int p = blockIdx.x / CL, tid = threadIdx.x;
     const long long mm = (long long)m * m;
     const float* G = A.G + (size_t)p * mm;
     const float* a = A.a + (size_t)p * m;
@@ -433,10 +508,14 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         sb += y;
     }
     float gmax = 0.f;
-    for (long long e = tid; e < mm; e += LOT_BT) {
-        const float c = fabsf(G[e]);
-        bad |= !(c < INFINITY);
-        gmax = fmaxf(gmax, c);
+    {
+        // the cost bound over this CTA's share of the instance's costs (all of them when CL = 1)
+        const long long e0 = mm * rank / CL, e1 = mm * (rank + 1) / CL;
+        for (long long e = e0 + tid; e < e1; e += LOT_BT) {
+            const float c = fabsf(G[e]);
+            bad |= !(c < INFINITY);
+            gmax = fmaxf(gmax, c);
+        }
     }
     bad = __syncthreads_or(bad);
     sa = lot_sum(sa, s_v);
@@ -446,13 +525,36 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     if ((tid & 31) == 0) s_v[tid >> 5] = gmax;
     __syncthreads();
     for (int k = 0; k < LOT_BW; ++k) gmax = fmaxf(gmax, (float)s_v[k]);
+    if constexpr (CL > 1) {
+        if (tid == 0) {
+            s_gmax = gmax;
+            s_bad = bad;
+            mbar_init(&mb_cand, CL - 1);
+            mbar_init(&mb_go, 1);
+            fence_mbar_init();
+        }
+        lot_cluster_sync();   // every CTA's share and barriers are ready
+        if (tid == 0) {
+            float g = 0.f;
+            int bd = 0;
+            for (int r = 0; r < CL; ++r) {
+                g = fmaxf(g, __int_as_float(lot_ld_remote32(lot_mapa(&s_gmax, (unsigned)r))));
+                bd |= lot_ld_remote32(lot_mapa(&s_bad, (unsigned)r));
+            }
+            s_v[LOT_BW] = g;
+            s_flag = bd;
+        }
+        __syncthreads();
+        gmax = (float)s_v[LOT_BW];
+        bad = s_flag;
+    }
     if (bad || !(sa > 0.0) || !(sb > 0.0)) {
         for (long long e = tid; e < mm; e += LOT_BT) S[e] = NAN;
         for (int i = tid; i < m; i += LOT_BT) {
             A.u[(size_t)p * m + i] = NAN;
             A.v[(size_t)p * m + i] = NAN;
         }
-        if (tid == 0) {
+        if (tid == 0 && rank == 0) {
             res->iters = 0;
             res->status = OT_ERR_ARG;
             res->marg_l1 = res->marg_l1_col = res->marg_l2_col = -1.0;
@@ -460,6 +562,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             res->reserved[0] = NAN;
             res->reserved[1] = 6.0;   // variant code: reduced LOT
         }
+        if constexpr (CL > 1) lot_cluster_sync();   // no CTA leaves while a peer may read it
         return;
     }
     const double ia = 1.0 / (sa * (double)A.N), ib = 1.0 / (sb * (double)A.N);
@@ -493,31 +596,37 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
     if (tid == 0) s_err = 0;
 
     // ---- pivots
-    const int npass = lot_price_passes(m);
-    const int rb = max(1, min(m, npass * LOT_PRICE_ARCS / m));   // rows per pricing step (rb m <= npass LOT_PRICE_ARCS)
+    const int npass = CL > 1 ? 1 : lot_price_passes(m);
+    const int rb = max(1, min(m, npass * LOT_PRICE_ARCS / m));   // rows per CTA and pricing step (rb m <= npass LOT_PRICE_ARCS)
     const int qstep = LOT_BT / m, rstep = LOT_BT - (LOT_BT / m) * m;
     const bool vec4 = (m & 3) == 0 && ((uintptr_t)A.G & 15) == 0;   // rows of whole, aligned float4s
     long long piv = 0;
     int status = OT_OK;
     int cursor = 0, scanned = 0;
-    for (;;) {
+    unsigned round = 0;
+    for (;; ++round) {
         __syncthreads();   // potentials and the previous reduction's results are settled
-        const int r1 = min(m, cursor + rb);
+        // this step's rows [cursor, rend), CTA `rank` taking the part [r0, r1)
+        const int rend = min(m, cursor + CL * rb);
+        const int per = (rend - cursor + CL - 1) / CL;
+        const int r0 = min(rend, cursor + rank * per), r1 = min(rend, r0 + per);
         long long best = 0x7fffffffffffffffll;
         int be = 0x7fffffff;
         const int e_end = r1 * m;
-        if (vec4) {
+        if (r0 >= r1) {
+            // no rows for this CTA in a short last step
+        } else if (vec4) {
             // all NP passes' loads in one unrolled sequence (independent, so all in flight)
             if (npass == 4)
-                lot_price_vec4<4>(G, word, m, cursor * m, e_end, sc, best, be);
+                lot_price_vec4<4>(G, word, m, r0 * m, e_end, sc, best, be);
             else if (npass == 2)
-                lot_price_vec4<2>(G, word, m, cursor * m, e_end, sc, best, be);
+                lot_price_vec4<2>(G, word, m, r0 * m, e_end, sc, best, be);
             else
-                lot_price_vec4<1>(G, word, m, cursor * m, e_end, sc, best, be);
+                lot_price_vec4<1>(G, word, m, r0 * m, e_end, sc, best, be);
         } else {
             for (int ps = 0; ps < npass; ++ps) {
                 // arcs e = cursor m + ps LOT_PRICE_ARCS + tid + k LOT_BT below e_end: a pass's loads issued up front
-                int e = cursor * m + ps * LOT_PRICE_ARCS + tid;
+                int e = r0 * m + ps * LOT_PRICE_ARCS + tid;
                 int r = e / m, j = e - r * m;
 #pragma unroll
                 for (int k = 0; k < LOT_PPT; ++k) {
@@ -540,16 +649,103 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             }
         }
         lot_argmin(best, be, s_q, s_i);
-        scanned += r1 - cursor;
-        cursor = r1 == m ? 0 : r1;
-        if (best >= 0) {
-            if (scanned >= m) break;   // a full pass found no improving arc: optimal
+        bool timed_out = false;
+        if constexpr (CL > 1) {
+            // the parts' candidates meet at the owner
+            if (rank != 0) {
+                if (tid == 0) {
+                    lot_st_remote64(lot_mapa(&s_cv[rank], 0u), best);
+                    lot_st_remote32(lot_mapa(&s_ce[rank], 0u), be);
+                    lot_remote_arrive(lot_mapa(&mb_cand, 0u));
+                }
+            } else {
+                if (tid == 0) {
+                    int to = !lot_wait_cluster(&mb_cand, round & 1u, A.timeout_ns);
+                    long long bv = best;
+                    int bi = be;
+                    for (int r = 1; r < CL; ++r) {
+                        const long long v = s_cv[r];
+                        const int i = s_ce[r];
+                        if (v < bv || (v == bv && i < bi)) {
+                            bv = v;
+                            bi = i;
+                        }
+                    }
+                    s_best = bv;
+                    s_be = bi;
+                    s_flag = to;
+                }
+                __syncthreads();
+                best = s_best;
+                be = s_be;
+                timed_out = s_flag != 0;
+            }
+        }
+        scanned += rend - cursor;
+        cursor = rend == m ? 0 : rend;
+        // the owner decides: 0 no improving arc in this step, 1 pivot, 2 stop
+        int dec = 0;
+        if (rank == 0) {
+            if (timed_out) {
+                status = OT_ERR_TIMEOUT;
+                dec = 2;
+            } else if (best >= 0) {
+                dec = scanned >= m ? 2 : 0;   // a full pass found no improving arc: optimal
+            } else if (piv >= A.max_pivots) {
+                status = OT_ERR_NOT_CONVERGED;
+                dec = 2;
+            } else {
+                dec = 1;
+                scanned = 0;
+            }
+        }
+        if (CL > 1 && rank != 0) {
+            // the owner's decision, and after a pivot the new potentials
+            if (tid == 0) {
+                int d = 2;
+                if (lot_wait_cluster(&mb_go, round & 1u, A.timeout_ns))
+                    d = lot_ld_remote32(lot_mapa(&s_dec, 0u));
+                s_flag = d;
+            }
+            __syncthreads();
+            dec = s_flag;
+            if (dec == 1) {
+                const unsigned mva = lot_mapa(&s_mv, 0u);
+                const int k = lot_ld_remote32(mva + offsetof(LotMove, k));
+                const int sz = lot_ld_remote32(mva + offsetof(LotMove, s));
+                const int lbase = lot_ld_remote32(mva + offsetof(LotMove, lbase));
+                const int lcap = lot_ld_remote32(mva + offsetof(LotMove, lcap));
+                const long long sig = lot_ld_remote64(mva + offsetof(LotMove, sigma));
+                if (k <= LOT_CPK && sz <= lcap) {
+                    const int nT = min(lot_ld_remote32(lot_mapa(&s_cnt, 0u)), lcap);
+                    const unsigned la = lot_mapa(chain + lbase, 0u);
+                    for (int i = tid; i < nT; i += LOT_BT) {
+                        const int x = lot_ld_remote16(la + 2u * (unsigned)i);
+                        if (x < V) word[x] += sig * (1ll << LOT_SB);
+                    }
+                } else {
+                    const unsigned wa = lot_mapa(word, 0u);
+                    for (int x = tid; x < V; x += LOT_BT) word[x] = lot_ld_remote64(wa + 8u * (unsigned)x);
+                }
+            }
+            if (dec == 2) break;
             continue;
         }
-        scanned = 0;
-        if (piv >= A.max_pivots) {
-            status = OT_ERR_NOT_CONVERGED;
-            break;
+        // the owner (or the only CTA)
+        auto release = [&](int d) {
+            if constexpr (CL > 1) {
+                if (tid == 0) s_dec = d;
+                __syncthreads();   // the decision, the move and T's list are written
+                if (tid == 0) {
+                    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+                    for (int r = 1; r < CL; ++r) lot_remote_arrive(lot_mapa(&mb_go, (unsigned)r));
+                }
+            }
+        };
+        if (dec != 1) {
+            release(dec);
+            if (dec == 2) break;
+            continue;
         }
         {
             // the next pricing block's costs into L2 while the pivot runs
@@ -567,6 +763,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         __syncthreads();
         if (s_err != OT_OK) {
             status = s_err;
+            release(2);
             break;
         }
         ++piv;
@@ -629,8 +826,13 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
                 }
             }
         }
+        release(1);
     }
     __syncthreads();
+    if (rank != 0) {
+        if constexpr (CL > 1) lot_cluster_sync();
+        return;
+    }
     // every potential against its parent arc: a wrong incremental update shows here
     {
         int bad_tree = 0;
@@ -701,6 +903,7 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         res->reserved[0] = Nd * dual;       // N (<alpha, u> + <beta, v>): equals value at optimality
         res->reserved[1] = 6.0;             // variant code: reduced LOT
     }
+    if constexpr (CL > 1) lot_cluster_sync();   // the peers no longer read this CTA
 }
 
 size_t lot_smem_bytes(int m) { return (size_t)22 * (2 * (size_t)m + 1) + 16; }
@@ -712,6 +915,65 @@ static_assert(2 * LOT_MAXM + 1 < (1 << LOT_SB), "subtree sizes fit their 14-bit 
 using namespace cyc;
 
 static size_t lot_a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int CL>
+static cudaError_t lot_prepare(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(lot_simplex_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+static void lot_cfg(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int CL, int count, size_t smem,
+                    cudaStream_t st) {
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(count * CL), 1, 1);
+    cfg.blockDim = dim3(LOT_BT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+
+// How many clusters of c CTAs (one instance each) can be resident at once.
+static bool lot_clusters_resident(int c, size_t smem, int* n) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    lot_cfg(cfg, attr, c, 1, smem, 0);
+    cudaError_t e;
+    switch (c) {
+        case 8: e = lot_prepare<8>(smem); if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(n, lot_simplex_kernel<8>, &cfg); break;
+        case 4: e = lot_prepare<4>(smem); if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(n, lot_simplex_kernel<4>, &cfg); break;
+        case 2: e = lot_prepare<2>(smem); if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(n, lot_simplex_kernel<2>, &cfg); break;
+        default: return false;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // an unsupported cluster shape only rules that size out
+        *n = 0;
+    }
+    return true;
+}
+
+static int lot_launch(int CL, int count, size_t smem, const LotArgs& A, cudaStream_t st) {
+    if (CL == 1) {
+        if (lot_prepare<1>(smem) != cudaSuccess) return OT_ERR_CUDA;
+        lot_simplex_kernel<1><<<count, LOT_BT, smem, st>>>(A);
+        return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+    }
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    lot_cfg(cfg, attr, CL, count, smem, st);
+    cudaError_t e;
+    switch (CL) {
+        case 8: e = cudaLaunchKernelEx(&cfg, lot_simplex_kernel<8>, A); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, lot_simplex_kernel<4>, A); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, lot_simplex_kernel<2>, A); break;
+        default: return OT_ERR_CUDA;
+    }
+    return e == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}
 
 extern "C" size_t ot_lot_workspace_bytes(int count, int m) {
     if (count <= 0 || m <= 0 || m > LOT_MAXM) return 0;
@@ -741,10 +1003,22 @@ extern "C" int ot_lot_reduced(int count, int m, int N, const float* a_base, cons
     A.v = v;
     A.res = out;
     A.sums = (double*)workspace;
+    A.timeout_ns = opt->timeout_ns ? opt->timeout_ns : 10000000000ull;
     const size_t smem = lot_smem_bytes(m);
-    if (cudaFuncSetAttribute(lot_simplex_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return OT_ERR_CUDA;
-    lot_simplex_kernel<<<count, LOT_BT, smem, (cudaStream_t)stream>>>(A);
-    return cudaGetLastError() == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+    // CTAs per instance: the largest of 8, 4, 2 for which every CTA prices a full block
+    // (CL LOT_PRICE_ARCS <= m^2) and all `count` clusters are resident at once; else one
+    const int cls[3] = {8, 4, 2};
+    int CL = 1;
+    if (!(opt->debug_flags & OT_DEBUG_NO_CLUSTER)) {
+        for (int c : cls) {
+            if ((long long)c * LOT_PRICE_ARCS > (long long)m * m) continue;
+            int ncl = 0;
+            if (!lot_clusters_resident(c, smem, &ncl)) return OT_ERR_CUDA;
+            if (ncl >= count) {
+                CL = c;
+                break;
+            }
+        }
+    }
+    return lot_launch(CL, count, smem, A, (cudaStream_t)stream);
 }

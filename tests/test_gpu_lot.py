@@ -126,6 +126,24 @@ def test_batch_of_problems_one_launch(cy):
         check_certificate(certificate(host(S[k]), host(u[k]), host(v[k]), alpha, beta, Go), 4)
 
 
+@pytest.mark.parametrize("m,N,count", [(1000, 10, 1), (1000, 10, 20), (302, 3, 2), (2500, 2, 1), (1502, 3, 1)])
+def test_cluster_pricing_matches_single_cta(cy, m, N, count):
+    """Several CTAs per instance (a cluster pricing a wider block) reach the same optimum as one
+    CTA per instance, with a valid certificate; m = 302 and 1502 take the scalar pricing path."""
+    ps = [I.paper_synthetic_problem(m, N, seed=11 + k) for k in range(count)]
+    G = torch.stack([cy.ot_fold_cost(cy.OT_MIN, m, N, C_base=dev(p.C_base))[0] for p in ps]).contiguous()
+    a = dev(np.stack([p.a_base for p in ps]))
+    b = dev(np.stack([p.b_base for p in ps]))
+    Sc, uc, vc, oc = cy.ot_lot_reduced(m, N, a, b, G, count=count)
+    Ss, us, vs, os_ = cy.ot_lot_reduced(m, N, a, b, G, count=count, single_cta=True)
+    rc, rs = cy.read_lot_results(oc, count), cy.read_lot_results(os_, count)
+    for k, p in enumerate(ps):
+        assert rc[k]["status"] == cy.OT_OK and rs[k]["status"] == cy.OT_OK
+        assert rc[k]["value"] == pytest.approx(rs[k]["value"], rel=1e-9)
+        alpha, beta = OS.base_marginals(p.a_base, p.b_base, N)
+        check_certificate(certificate(host(Sc[k]), host(uc[k]), host(vc[k]), alpha, beta, host(G[k])), N)
+
+
 @pytest.mark.parametrize("m", [64, 1000])
 def test_uniform_marginals_is_assignment(cy, m):
     """Uniform marginals: by Birkhoff-von Neumann the LP optimum is an assignment (many degenerate pivots)."""
