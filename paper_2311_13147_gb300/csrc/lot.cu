@@ -81,6 +81,7 @@ __device__ __forceinline__ int lot_price_passes(int m) { return m >= 4000 ? 4 : 
 
 #define LOT_NPT ((2 * LOT_MAXM + 1 + LOT_BT - 1) / LOT_BT)   // tree nodes per thread, at most
 #define LOT_CPK 256                                          // reversed-path ranges kept packed for the move pass
+#define LOT_CLUSTER_MIN_M 800   // clusters per instance from this m (Table 1: 37.5 vs 41.5 ms at m = 1000; slower at m <= 500)
 
 struct LotArgs {
     int count, m, N;
@@ -1005,11 +1006,12 @@ extern "C" int ot_lot_reduced(int count, int m, int N, const float* a_base, cons
     A.sums = (double*)workspace;
     A.timeout_ns = opt->timeout_ns ? opt->timeout_ns : 10000000000ull;
     const size_t smem = lot_smem_bytes(m);
-    // CTAs per instance: the largest of 8, 4, 2 for which every CTA prices a full block
-    // (CL LOT_PRICE_ARCS <= m^2) and all `count` clusters are resident at once; else one
+    // CTAs per instance: from m = LOT_CLUSTER_MIN_M (below it a pivot is cheaper than the
+    // hand-offs between CTAs), the largest of 8, 4, 2 for which every CTA prices a full
+    // block (CL LOT_PRICE_ARCS <= m^2) and all `count` clusters are resident at once; else one
     const int cls[3] = {8, 4, 2};
     int CL = 1;
-    if (!(opt->debug_flags & OT_DEBUG_NO_CLUSTER)) {
+    if (!(opt->debug_flags & OT_DEBUG_NO_CLUSTER) && m >= LOT_CLUSTER_MIN_M) {
         for (int c : cls) {
             if ((long long)c * LOT_PRICE_ARCS > (long long)m * m) continue;
             int ncl = 0;
