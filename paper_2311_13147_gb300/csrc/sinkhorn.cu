@@ -2407,11 +2407,15 @@ static const int kFusedMaxCols = OT_BLOCK * 16;
 static const int kFusedMaxRowsPerBlock = 128;
 static const size_t kSmemBudget = 200 * 1024;
 
+// Blocks of the persistent solvers: about four rows each, at most one per SM, and at most
+// 128 up to 1024 rows, where the sweep is one band per block and the column exchange
+// dominates (m = 1024 on this GPU: 6.48 us per sweep with 128 blocks, 6.91 with 152).
 static int solver_grid(int M) {
     int sms = device_sms();
     if (sms <= 0) return 0;
     int g = (M + 3) / 4;
     if (g > sms) g = sms;
+    if (M <= 1024 && g > 128) g = 128;
     if (g < 1) g = 1;
     return g;
 }
