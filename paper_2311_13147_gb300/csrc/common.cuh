@@ -50,23 +50,42 @@ __device__ __forceinline__ int ld_volatile_int(const int* p) {
 // Control block at the start of every persistent-kernel workspace.  The host
 // zeroes it (cudaMemsetAsync) before each launch.
 struct Ctrl {
-    unsigned count;      // monotonic barrier arrival counter
-    unsigned gen;        // unused (kept for layout)
+    unsigned count;      // monotonic barrier arrival counter (low half of the barrier word)
+    unsigned gen;        // error marks (high half of the barrier word: nonzero once an error is recorded)
     int status;          // first device-side error (OT_ERR_*), 0 if none
     int flag;            // kernel-specific shared flag
     unsigned long long pad[6];
 };
 static_assert(sizeof(Ctrl) == 64, "Ctrl must stay 64 bytes");
 
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// The barrier word: count (arrivals) and gen (error marks) as one 64-bit location, so a
+// single acquire load tells a waiting block both whether the barrier completed and
+// whether an error was recorded.
+__device__ __forceinline__ unsigned long long* ctrl_word(Ctrl* c) {
+    return reinterpret_cast<unsigned long long*>(&c->count);
+}
+__device__ __forceinline__ void red_release_add64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Records the first device-side error (its code in status) and marks the barrier word,
+// so that every block waiting at a grid barrier, now or later, leaves at once.
+__device__ __forceinline__ void set_status(Ctrl* c, int st) {
+    atomicCAS(&c->status, 0, st);
+    red_release_add64(ctrl_word(c), 1ull << 32);
 }
 
 // Grid-wide barrier for a cooperative launch.  `epoch` counts the barriers this
 // block has passed (start at 0, the caller keeps it): arrivals accumulate on a
 // monotonic counter and barrier k completes when it reaches nblocks * (k + 1).
-// Returns false (in every thread of the block) if the wait expired or another
-// block already recorded an error; the caller must then leave the kernel.
+// Returns false (in every thread of the block) if the wait expired or an error is
+// marked (checked by the same load that observes the arrivals: no extra round trip);
+// the caller must then leave the kernel.
 __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned long long timeout_ns,
                                           unsigned& epoch) {
     __shared__ int s_ok;
@@ -75,18 +94,22 @@ __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned lo
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned target = nblocks * epoch;
-        red_release_add(&c->count, 1u);
-        if ((int)(ld_acquire(&c->count) - target) < 0) {
+        unsigned long long* wd = ctrl_word(c);
+        red_release_add64(wd, 1ull);
+        unsigned long long w = ld_acquire64(wd);
+        if ((int)((unsigned)w - target) < 0 && (w >> 32) == 0) {
             const unsigned long long t0 = globaltimer();
-            while ((int)(ld_acquire(&c->count) - target) < 0) {
+            for (;;) {
+                w = ld_acquire64(wd);
+                if ((int)((unsigned)w - target) >= 0 || (w >> 32) != 0) break;
                 if (globaltimer() - t0 > timeout_ns) {
-                    atomicCAS(&c->status, 0, OT_ERR_TIMEOUT);
+                    set_status(c, OT_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
             }
         }
-        if (ld_volatile_int(&c->status) != 0) ok = 0;
+        if ((w >> 32) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -148,7 +171,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return true;
 }
 
-__device__ __forceinline__ void set_status(Ctrl* c, int st) { atomicCAS(&c->status, 0, st); }
 
 // Fault injection for tests: instead of arriving at the barrier, wait (bounded)
 // until another block has recorded an error, then report failure.
@@ -158,7 +180,7 @@ __device__ __forceinline__ bool withhold_arrival(Ctrl* c, unsigned long long tim
         const unsigned long long t0 = globaltimer();
         while (ld_volatile_int(&c->status) == 0) {
             if (globaltimer() - t0 > 4 * timeout_ns + 1000000ull) {
-                atomicCAS(&c->status, 0, OT_ERR_TIMEOUT);
+                set_status(c, OT_ERR_TIMEOUT);
                 break;
             }
             __nanosleep(100);
