@@ -170,8 +170,9 @@ class ClockSampler:
 def profile_traffic(kernel_file: str, source: str):
     """DRAM traffic per launch recorded from an ncu capture in profiles/, if still current.
 
-    The summary carries the sha256 of the kernel source it was taken on; a
-    changed source means the counters no longer describe this kernel (None).
+    The summary carries the sha256 of the kernel source it was taken on (and of the
+    shared device header, when recorded); a changed source means the counters no
+    longer describe this kernel (None).
     """
     import hashlib
     try:
@@ -184,6 +185,10 @@ def profile_traffic(kernel_file: str, source: str):
                 fields[k.strip()] = v.strip()
         if fields.get("source_sha256") != sha:
             return None
+        if "header_sha256" in fields:   # the shared device header the kernel was built with
+            hdr = open(os.path.join(ROOT, "paper_2311_13147_gb300", "csrc", "common.cuh"), "rb").read()
+            if fields["header_sha256"] != hashlib.sha256(hdr).hexdigest():
+                return None
         return float(fields["dram_bytes_per_launch"])
     except Exception:
         return None
