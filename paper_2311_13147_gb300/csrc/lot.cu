@@ -35,9 +35,8 @@
 //           the paths are recorded, and the rest of the pivot runs over them
 //           in parallel.  The flow on the cycle's backward arcs bounds the
 //           step, and of the blocking arcs the last one met when going round
-//           the cycle from that ancestor leaves (the
-//           rule that keeps the tree strongly feasible, so degenerate pivots
-//           cannot cycle); the cut-off subtree T is re-hung from the entering
+//           the cycle from that ancestor leaves (the rule that keeps the tree
+//           strongly feasible, so degenerate pivots cannot cycle); the cut-off subtree T is re-hung from the entering
 //           arc by reversing the parent pointers on the path between them,
 //           and only the subtree sizes on the cycle change outside T;
 //  duals    every node's potential is the signed sum of arc costs on its path
@@ -58,9 +57,10 @@
 // the parent and the arc's direction in 16 bits (an original arc is fixed by
 // its two ends, and points from the source to the sink; an arc to the root is
 // artificial), the preorder position, and one slot of the pivot's path buffer.
-// A launch solves `count` problems of one size at once.  Every loop has a bound; a tree found inconsistent (also by a
-// check of every potential against its parent arc after the last pivot) ends
-// the solve with OT_ERR_NONFINITE instead of looping.
+// A launch solves `count` problems of one size at once.  Every loop has a bound;
+// a tree found inconsistent (also by a check of every potential against its
+// parent arc after the last pivot) ends the solve with OT_ERR_NONFINITE instead
+// of looping.
 #include <math.h>
 #include <string.h>
 
@@ -123,11 +123,6 @@ __device__ __forceinline__ long long lot_ld_remote64(unsigned addr) {
 __device__ __forceinline__ int lot_ld_remote32(unsigned addr) {
     int v;
     asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned short lot_ld_remote16(unsigned addr) {
-    unsigned short v;
-    asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
     return v;
 }
 __device__ __forceinline__ void lot_st_remote64(unsigned addr, long long v) {
@@ -701,28 +696,48 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
             }
         }
         if (CL > 1 && rank != 0) {
-            // the owner's decision, and after a pivot the new potentials
+            // the owner's decision, and after a pivot the new potentials.  Thread 0 alone reads
+            // the decision and the move's fields from the owner (one round trip, and no
+            // thousand-fold requests at the owner's shared memory); the list of T's nodes is read
+            // in 4-byte words of two entries (the path buffer starts at byte 20 (2m + 1), a
+            // multiple of 4 but not of 8, and has 16 spare bytes after it).
             if (tid == 0) {
                 int d = 2;
-                if (lot_wait_cluster(&mb_go, round & 1u, A.timeout_ns))
+                if (lot_wait_cluster(&mb_go, round & 1u, A.timeout_ns)) {
                     d = lot_ld_remote32(lot_mapa(&s_dec, 0u));
+                    if (d == 1) {
+                        const unsigned mva = lot_mapa(&s_mv, 0u);
+                        const int k = lot_ld_remote32(mva + offsetof(LotMove, k));
+                        const int sz = lot_ld_remote32(mva + offsetof(LotMove, s));
+                        const int lbase = lot_ld_remote32(mva + offsetof(LotMove, lbase));
+                        const int lcap = lot_ld_remote32(mva + offsetof(LotMove, lcap));
+                        const long long sig = lot_ld_remote64(mva + offsetof(LotMove, sigma));
+                        const int cnt = lot_ld_remote32(lot_mapa(&s_cnt, 0u));
+                        s_mv.sigma = sig;
+                        s_mv.lbase = lbase;
+                        // list length, or -1: the move took the full pass, copy every potential
+                        s_mv.k = (k <= LOT_CPK && sz <= lcap) ? min(cnt, lcap) : -1;
+                    }
+                }
                 s_flag = d;
             }
             __syncthreads();
             dec = s_flag;
             if (dec == 1) {
-                const unsigned mva = lot_mapa(&s_mv, 0u);
-                const int k = lot_ld_remote32(mva + offsetof(LotMove, k));
-                const int sz = lot_ld_remote32(mva + offsetof(LotMove, s));
-                const int lbase = lot_ld_remote32(mva + offsetof(LotMove, lbase));
-                const int lcap = lot_ld_remote32(mva + offsetof(LotMove, lcap));
-                const long long sig = lot_ld_remote64(mva + offsetof(LotMove, sigma));
-                if (k <= LOT_CPK && sz <= lcap) {
-                    const int nT = min(lot_ld_remote32(lot_mapa(&s_cnt, 0u)), lcap);
-                    const unsigned la = lot_mapa(chain + lbase, 0u);
-                    for (int i = tid; i < nT; i += LOT_BT) {
-                        const int x = lot_ld_remote16(la + 2u * (unsigned)i);
-                        if (x < V) word[x] += sig * (1ll << LOT_SB);
+                const long long sig = s_mv.sigma;
+                const int nT = s_mv.k, lbase = s_mv.lbase;
+                if (nT >= 0) {
+                    // entries [lbase, lbase + nT) of the owner's path buffer, by 4-byte words
+                    const int w0 = lbase >> 1, w1 = (lbase + nT + 1) >> 1;
+                    const unsigned ca = lot_mapa(chain, 0u);
+                    for (int wi = w0 + tid; wi < w1; wi += LOT_BT) {
+                        const unsigned v = (unsigned)lot_ld_remote32(ca + 4u * (unsigned)wi);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int i = 2 * wi + h;
+                            const int x = (int)((v >> (16 * h)) & 0xffffu);
+                            if (i >= lbase && i < lbase + nT && x < V) word[x] += sig * (1ll << LOT_SB);
+                        }
                     }
                 } else {
                     const unsigned wa = lot_mapa(word, 0u);
