@@ -379,9 +379,10 @@ size_t ot_kdomain_workspace_bytes(int m);
  * ot_kdomain_solve -- Algorithm 2 in scaling form (Eq.
  * optimal_f_sinkhorn_logdomain exponentiated: U = alpha ./ (K V),
  * V = beta ./ (K^T U), K = exp(-G / eps)) for nrhs <= 64 histogram pairs that
- * share one folded cost G.  K, K^T and the scalings are BF16 operands of
- * tcgen05 tensor-core products with FP32 accumulation; the scalings are kept
- * in FP32 between products.  Runs exactly `iters` iterations from V = 1 (no
+ * share one folded cost G.  K, K^T (tile-major) and the scalings are BF16
+ * operands of tcgen05 tensor-core products with FP32 accumulation; each
+ * product applies its scaling update in its own epilogue, and the scalings
+ * are kept in FP32 between products.  Runs exactly `iters` iterations from V = 1 (no
  * stopping rule: BF16 bounds the reachable accuracy near 1e-3; polish the
  * result with ot_batch_solve, warm-started from z).
  *  G: [m][ld] FP32 device, ld >= m.  a_hist, b_hist: [nrhs][m] FP32 device,
@@ -404,9 +405,12 @@ int ot_kdomain_status(const void* workspace, int m, int* status, void* stream);
  * ot_kdomain_product -- the tensor-core product used by ot_kdomain_solve:
  * Dt[n][i] = sum_k A[i][k] X[n][k] for n < 64, i < mp; A [mp][mp] BF16,
  * X [64][mp] BF16, Dt [64][mp] FP32 (device, 16-byte aligned; mp a multiple
- * of 128, <= 16384).  workspace: >= ot_kdomain_workspace_bytes(mp) bytes
- * (256-byte aligned; holds the partial products of the reduction slices).
- * Blocks until done; returns OT_ERR_TIMEOUT if a device wait expired.
+ * of 128, <= 16384; A row-major).  The reduction is split over the CTAs of
+ * a thread-block cluster and summed in distributed shared memory, so no
+ * partial product reaches global memory.  workspace: >=
+ * ot_kdomain_workspace_bytes(mp) bytes, 256-byte aligned (kept for the
+ * interface; the product needs none of it).  Blocks until done; returns
+ * OT_ERR_TIMEOUT if a device wait expired.
  */
 int ot_kdomain_product(int mp, const void* A, const void* X, float* Dt, void* workspace, size_t ws_bytes,
                        void* stream);
