@@ -467,7 +467,9 @@ size_t ot_lot_workspace_bytes(int count, int m);
  *  opt: max_iter is the pivot cap per problem (>= 1); timeout_ns bounds each
  *     wait between the CTAs that share one problem (0 = 10 s; an expired wait
  *     ends that problem with OT_ERR_TIMEOUT); debug_flags bit 2
- *     (OT_DEBUG_NO_CLUSTER) keeps one thread block per problem.  When the
+ *     (OT_DEBUG_NO_CLUSTER) keeps one thread block per problem, bit 0
+ *     (OT_DEBUG_WITHHOLD_ARRIVAL, failure-detection tests) makes the second CTA
+ *     of each cluster withhold its first candidate, so the owner's wait expires.  When the
  *     launch fits, each problem gets a thread-block cluster of 2, 4 or 8 CTAs
  *     that price separate parts of a wider block of arcs (one owns the tree);
  *     the other fields are not used.

@@ -95,6 +95,7 @@ struct LotArgs {
     ot_result* res;        // [count]
     double* sums;          // [count][2m] row and column sums of the returned plan (workspace)
     unsigned long long timeout_ns;   // bound on each wait between the CTAs of a cluster
+    int debug_flags;                 // OT_DEBUG_WITHHOLD_ARRIVAL: CTA 1 withholds its first candidate
 };
 
 // ---- thread-block cluster helpers (one instance per cluster of CL CTAs)
@@ -649,7 +650,10 @@ __global__ void __launch_bounds__(LOT_BT, 1) lot_simplex_kernel(const __grid_con
         if constexpr (CL > 1) {
             // the parts' candidates meet at the owner
             if (rank != 0) {
-                if (tid == 0) {
+                // (fault injection for tests: CTA 1 never hands in its first candidate, so the
+                // owner's bounded wait expires and the solve reports OT_ERR_TIMEOUT)
+                const bool withhold = (A.debug_flags & OT_DEBUG_WITHHOLD_ARRIVAL) && rank == 1 && round == 0;
+                if (tid == 0 && !withhold) {
                     lot_st_remote64(lot_mapa(&s_cv[rank], 0u), best);
                     lot_st_remote32(lot_mapa(&s_ce[rank], 0u), be);
                     lot_remote_arrive(lot_mapa(&mb_cand, 0u));
@@ -1020,6 +1024,7 @@ extern "C" int ot_lot_reduced(int count, int m, int N, const float* a_base, cons
     A.res = out;
     A.sums = (double*)workspace;
     A.timeout_ns = opt->timeout_ns ? opt->timeout_ns : 10000000000ull;
+    A.debug_flags = opt->debug_flags;
     const size_t smem = lot_smem_bytes(m);
     // CTAs per instance: from m = LOT_CLUSTER_MIN_M (below it a pivot is cheaper than the
     // hand-offs between CTAs), the largest of 8, 4, 2 for which every CTA prices a full

@@ -558,11 +558,13 @@ def lot_workspace(count: int, m: int, device) -> torch.Tensor:
 
 
 def ot_lot_reduced(m: int, N: int, a_base, b_base, G, count: int = 1, max_pivots: Optional[int] = None,
-                   S=None, u=None, v=None, out=None, ws=None, stream=None, single_cta: bool = False):
+                   S=None, u=None, v=None, out=None, ws=None, stream=None, single_cta: bool = False,
+                   debug_flags: int = 0, timeout_ns: int = 0):
     """Small LOT of Theorem 1 by the network simplex: S [count][m][m] FP32, duals u, v [count][m] FP64.
 
     a_base, b_base: [count][m] (or [m] when count = 1); G: [count][m][m] (or [m][m]), the min-fold.
     single_cta: one thread block per instance even where a cluster of them would fit.
+    debug_flags, timeout_ns: as in ot_options (failure-detection tests).
     Returns (S, u, v, out) with out a [count] result buffer (value = <G, S>, reserved[0] = dual value).
     """
     dev = G.device
@@ -573,7 +575,7 @@ def ot_lot_reduced(m: int, N: int, a_base, b_base, G, count: int = 1, max_pivots
         out = torch.zeros((count, ctypes.sizeof(ot_result)), dtype=torch.uint8, device=dev)
     ws = lot_workspace(count, m, dev) if ws is None else ws
     opt = options(1.0, max_iter=int(max_pivots if max_pivots is not None else 100 * m + 10000),
-                  debug_flags=OT_DEBUG_NO_CLUSTER if single_cta else 0)
+                  debug_flags=(OT_DEBUG_NO_CLUSTER if single_cta else 0) | int(debug_flags), timeout_ns=int(timeout_ns))
     code = _lot_lib().ot_lot_reduced(int(count), int(m), int(N), _ptr(a_base), _ptr(b_base), _ptr(G),
                                      ctypes.byref(opt), _ptr(S), _ptr(u), _ptr(v), _ptr(out), _ptr(ws), ws.numel(),
                                      _stream(stream))

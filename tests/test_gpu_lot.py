@@ -144,6 +144,25 @@ def test_cluster_pricing_matches_single_cta(cy, m, N, count):
         check_certificate(certificate(host(Sc[k]), host(uc[k]), host(vc[k]), alpha, beta, host(G[k])), N)
 
 
+def test_cluster_wait_expires_and_reports_timeout(cy):
+    """A CTA of the cluster that never hands in its candidate (fault injection on the host's
+    request, no GPU fault): the owner's bounded wait expires, every CTA leaves, the status is
+    OT_ERR_TIMEOUT, and the next solve on the same buffers is normal."""
+    p = I.paper_synthetic_problem(1000, 10, seed=5)
+    G, _ = cy.ot_fold_cost(cy.OT_MIN, p.m, p.N, C_base=dev(p.C_base))
+    a, b = dev(p.a_base), dev(p.b_base)
+    S, u, v, out = cy.ot_lot_reduced(p.m, p.N, a, b, G, debug_flags=cy.OT_DEBUG_WITHHOLD_ARRIVAL,
+                                     timeout_ns=20_000_000)
+    r = cy.read_lot_results(out, 1)[0]
+    assert r["status"] == cy.OT_ERR_TIMEOUT
+    S, u, v, out = cy.ot_lot_reduced(p.m, p.N, a, b, G, S=S, u=u, v=v, out=out)
+    r = cy.read_lot_results(out, 1)[0]
+    assert r["status"] == cy.OT_OK
+    Go, _ = OS.fold_min(p.C_base.astype(np.float64))
+    alpha, beta = OS.base_marginals(p.a_base, p.b_base, p.N)
+    assert r["value"] == pytest.approx(p.N * OL.highs_lp(alpha, beta, Go)["value"], rel=1e-6)
+
+
 @pytest.mark.parametrize("m", [64, 1000])
 def test_uniform_marginals_is_assignment(cy, m):
     """Uniform marginals: by Birkhoff-von Neumann the LP optimum is an assignment (many degenerate pivots)."""
