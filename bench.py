@@ -572,12 +572,14 @@ def run_ours_batch(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-                     "kernel": "batch_solve_kernel (one FP32 read of every active problem's folded cost per sweep)",
+                     "kernel": "batch_solve_kernel, its two launches (one FP32 read of every active problem's "
+                               "folded cost per sweep)",
                      "solve_ms": solve_ms, "alg_bytes": alg_bytes},
         "e2e": {"value": world * count * args.steps / (t_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
-        "kernels_per_step": ["batch_fold_kernel", "batch_solve_kernel"],
+        # the fold, then the solver once for the problems with two rows per chunk and once for those with three
+        "gpu_launches": 3 * args.steps,
+        "kernels_per_step": ["batch_fold_kernel", "batch_solve_kernel<2, 2>", "batch_solve_kernel<2, 3>"],
         "clocks": clk,
     }
     return out, (probs, iters)
@@ -748,7 +750,8 @@ def run_ours_precision(args, rank, world, local_rank):
                      "ms_per_bf16_iter": per_iter_ms},
         # per cost and step: the fold, the kernel-domain solve (K and K^T, prep, 2 launches per
         # BF16 iteration (each product applies its scaling update), the log of the scalings) and the polish
-        "gpu_launches": args.steps * len(sbs) * (1 + 3 + 2 * PRECISION_BF16_ITERS + 1),
+        # (two solver launches: one per rows-per-chunk class, the one without problems leaves at once)
+        "gpu_launches": args.steps * len(sbs) * (1 + 3 + 2 * PRECISION_BF16_ITERS + 2),
         "clocks": clk,
     }
     # objective errors against the FP64 oracle on the two smallest costs (4 pairs each)
@@ -1077,7 +1080,8 @@ def batch_sweep(args, local_rank):
     out = {"workload": "batch_512_ring_N2-8_n1024-16384", "count": len(probs),
            "sum_m2": int(sum(p.m * p.m for p in probs)), "launch_config": code, "solve_ms": solve_ms,
            "alg_bytes": alg, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
-           "peak_source": peak_src, "kernel": "batch_solve_kernel", "sweeps_total": int((iters + 1).sum()),
+           "peak_source": peak_src, "kernel": "batch_solve_kernel (two launches: two and three rows per chunk)",
+           "sweeps_total": int((iters + 1).sum()),
            "max_marg_l1": max(r["marg_l1"] for r in res), "clocks": clk}
     del bs
     torch.cuda.empty_cache()

@@ -290,7 +290,8 @@ size_t ot_batch_workspace_bytes(int count, long long total_m);
 /*
  * ot_batch_prepare -- copy the problem table into the workspace (outside any
  * stream capture).  descs is HOST memory (count entries); it is not read
- * after the call returns.  The prefix tables the solver needs are built here.
+ * after the call returns.  The header the solver reads (sizes, and the number
+ * of problems of each rows-per-chunk class) is written here.
  */
 int ot_batch_prepare(const ot_problem_desc* descs, int count, void* workspace, size_t ws_bytes, void* stream);
 
@@ -304,8 +305,11 @@ int ot_batch_fold(int count, const float* points, float* G_all, void* workspace,
 
 /*
  * ot_batch_solve -- cyclic Sinkhorn (Algorithm 2) on every problem of a
- * prepared batch in ONE persistent cooperative launch (capturable in a CUDA
- * graph: it only enqueues kernels and memsets).  Each sweep re-balances the
+ * prepared batch in two persistent cooperative launches (capturable in a CUDA
+ * graph: it only enqueues kernels and memsets): one for the problems whose
+ * rows fill three float4 slots per thread of their group (processed three
+ * rows per group at a time), one for the others (two rows at a time); a
+ * launch without problems of its kind returns at once.  Each sweep re-balances the
  * rows of the still-active problems over the blocks; a problem leaves the
  * batch when its full-scale row L1 error <= opt->tol_l1 (its state is then
  * frozen) or after opt->max_iter iterations.  opt->eps is ignored (per
@@ -320,8 +324,8 @@ int ot_batch_fold(int count, const float* points, float* G_all, void* workspace,
  * the tolerance.
  * G_all must be 16-byte aligned (cost rows are streamed with bulk copies);
  * otherwise OT_ERR_ARG.  A copy or grid barrier that does not complete within
- * opt->timeout_ns (0: 10 s) ends the launch with OT_ERR_TIMEOUT in every
- * result (iters = -1).  The problems of one prepared workspace must not be
+ * opt->timeout_ns (0: 10 s) ends that launch with OT_ERR_TIMEOUT in the
+ * results of its problems (iters = -1).  The problems of one prepared workspace must not be
  * solved on two streams at once.
  */
 int ot_batch_solve(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,

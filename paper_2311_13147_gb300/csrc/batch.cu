@@ -67,6 +67,7 @@ struct BatchArgs {
     int warm;
     int gs_shift;                  // group-size policy (0: tight, 1: one size larger)
     int check_every;               // the stopping rule is applied every check_every iterations
+    const int* nrows;              // [2][2] problems per group-size shift and rows per chunk (null: not counted)
     double* w_out;
     double* z_out;
     ot_result* res;
@@ -87,22 +88,32 @@ struct BatchArgs {
     float* R;                      // [total_m] column sums
 };
 
-// Dynamic shared memory of the solver: OT_STAGES_MAX chunk stages (two rows per
-// group, and their rows' scalars) filled by bulk copies, the current problem's
-// staged column data, prefix sums, block sizes and active flags.
+// Rows per group and chunk: three when a thread's row slice fills three float4
+// slots (the per-chunk costs that do not grow with the row, the group reduction
+// above all, are then shared by three rows), otherwise two.  A stage holds the
+// larger of two rows of 8192 and three of 6144 floats.
+#define OT_STAGE_FLOATS (3 * 3 * OT_BATCH_MAXM / 4)
+#define OT_RSC_STAGE (3 * OT_BW)   // row scalars per stage (float4)
+static_assert(OT_STAGE_FLOATS >= 2 * OT_BATCH_MAXM, "a stage holds two of the longest rows");
+
+// Dynamic shared memory of the solver: OT_STAGES_MAX chunk stages (two or three
+// rows per group, and their rows' scalars) filled by bulk copies, the current
+// problem's staged column data, prefix sums, block sizes, row weights and active
+// flags.
 constexpr size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 struct BatchSmem {
     static constexpr size_t stage = 0;
-    static constexpr size_t rsc = a128(stage + sizeof(float) * 2 * OT_BATCH_MAXM * OT_STAGES_MAX);
-    static constexpr size_t gc = a128(rsc + sizeof(float4) * 2 * OT_BW * OT_STAGES_MAX);
+    static constexpr size_t rsc = a128(stage + sizeof(float) * OT_STAGE_FLOATS * OT_STAGES_MAX);
+    static constexpr size_t gc = a128(rsc + sizeof(float4) * OT_RSC_STAGE * OT_STAGES_MAX);
     static constexpr size_t cf = a128(gc + sizeof(float) * OT_BATCH_MAXM);
     static constexpr size_t pref = a128(cf + sizeof(float) * OT_BATCH_MAXM);
     static constexpr size_t msz = a128(pref + sizeof(long long) * (OT_BATCH_MAX + 1));
-    static constexpr size_t act = a128(msz + sizeof(int) * OT_BATCH_MAX);
-    static constexpr size_t rw = a128(act + sizeof(int) * OT_BATCH_MAX);
-    static constexpr size_t total = a128(rw + sizeof(int) * OT_BATCH_MAX);
+    static constexpr size_t rw = a128(msz + sizeof(unsigned short) * OT_BATCH_MAX);
+    static constexpr size_t act = a128(rw + sizeof(unsigned short) * OT_BATCH_MAX);
+    static constexpr size_t total = a128(act + sizeof(unsigned char) * OT_BATCH_MAX);
 };
 static_assert(4 * OT_BV * OT_BT == OT_BATCH_MAXM, "a full block covers the longest row");
+static_assert(OT_BATCH_MAXM <= 65535, "block sizes are kept as 16-bit integers");
 static_assert(BatchSmem::total + 2048 <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void red_add_f32(float* p, float v) {
@@ -137,12 +148,15 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
     return d;
 }
 
-// Compensated (Kahan) addition on both lanes of the contribution u0 e0 + u1 e1:
-// sum - nc carries the running total of the added values to about one rounding,
-// however many rows a thread accumulates (nc is the negated compensation, so the
-// contribution and the compensation enter through two FMAs).
-__device__ __forceinline__ void kahan2(f32x2& sum, f32x2& nc, f32x2 u0, f32x2 e0, f32x2 u1, f32x2 e1) {
-    const f32x2 y = fma2(u1, e1, fma2(u0, e0, nc));
+// Compensated (Kahan) addition on both lanes of the contribution sum_r u_r e_r
+// of a chunk's rows: sum - nc carries the running total of the added values to
+// about one rounding, however many rows a thread accumulates (nc is the negated
+// compensation, so the contributions and the compensation enter through FMAs).
+template <int R>
+__device__ __forceinline__ void kahan_rows(f32x2& sum, f32x2& nc, const f32x2 (&u)[R], const f32x2 (&e)[R]) {
+    f32x2 y = nc;
+#pragma unroll
+    for (int r = 0; r < R; ++r) y = fma2(u[r], e[r], y);
     const f32x2 t = add2(sum, y);
     nc = sub2(y, sub2(t, sum));
     sum = t;
@@ -175,21 +189,31 @@ __host__ __device__ __forceinline__ int group_size(int ld, int shift) {
     return gs < OT_BT ? gs : OT_BT;
 }
 
+// Float4 slots of a row that each thread of its group covers (1 .. OT_BV).
+__host__ __device__ __forceinline__ int row_slots(int ld, int shift) {
+    const int gs = group_size(ld, shift);
+    return (ld + 4 * gs - 1) / (4 * gs);
+}
+
+// Rows per group and chunk (see OT_STAGE_FLOATS).
+__host__ __device__ __forceinline__ int chunk_rows(int slots) { return slots == 3 ? 3 : 2; }
+
 // Estimated cost of one row of a problem, the unit of the row phase's work split:
-// a chunk costs its groups a fixed part plus a part per filled float4 slot, and
-// holds two rows per group, so a row costs GS (OT_ROW_FIXED + slots) / 2 thread
-// slots (the factor 1/2 is common to all problems and dropped).  Splitting by bytes
-// instead would give blocks with short rows more chunks than the others.
+// a chunk costs its group a fixed part (OT_ROW_FIXED slots) plus half a slot per
+// filled float4 slot and row, and holds R rows per group, so a row costs
+// GS (OT_ROW_FIXED / R + slots / 2) thread slots; times 6 to stay integral.
+// Splitting by bytes instead would give blocks with short rows more chunks than
+// the others.
 __host__ __device__ __forceinline__ int row_weight(int ld, int shift) {
     const int gs = group_size(ld, shift);
-    const int slots = (ld + 4 * gs - 1) / (4 * gs);
-    return gs * (OT_ROW_FIXED + slots);
+    const int slots = row_slots(ld, shift);
+    return gs * (6 * OT_ROW_FIXED / chunk_rows(slots) + 3 * slots);
 }
 
 // Block-wide exclusive scan of the per-problem weights (m x row weight for rows,
 // m for columns; 0 for finished problems) into s_pref[0..count].
-__device__ void batch_prefix(int count, const int* s_m, const int* s_rw, const int* act, bool rows, long long* s_pref,
-                             long long* s_wsum) {
+__device__ void batch_prefix(int count, const unsigned short* s_m, const unsigned short* s_rw,
+                             const unsigned char* act, bool rows, long long* s_pref, long long* s_wsum) {
     // each thread sums a contiguous chunk, then a warp scan of the chunk sums
     const int tid = threadIdx.x;
     const int per = (count + OT_BT - 1) / OT_BT;
@@ -255,35 +279,50 @@ __device__ __forceinline__ void group_barrier(int gs, int q) {
     else __syncwarp();
 }
 
-// All-reduce of two values (the two rows of a chunk) over a group.
-template <bool MAX>
-__device__ __forceinline__ void group_allreduce2(float& v0, float& v1, int gs, float* s_part, int& parity) {
+// All-reduce of R values (the rows of a chunk) over a group.  A warp's partials
+// sit in one 8-byte (two rows) or 16-byte (three rows) slot of s_part per warp.
+template <bool MAX, int R>
+__device__ __forceinline__ void group_allreduce(float (&v)[R], int gs, float* s_part, int& parity) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const float a = __shfl_xor_sync(0xffffffffu, v0, o), b = __shfl_xor_sync(0xffffffffu, v1, o);
-        v0 = MAX ? fmaxf(v0, a) : v0 + a;
-        v1 = MAX ? fmaxf(v1, b) : v1 + b;
+        float a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = __shfl_xor_sync(0xffffffffu, v[r], o);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = MAX ? fmaxf(v[r], a[r]) : v[r] + a[r];
     }
     if (gs > 32) {
         const int tid = threadIdx.x, lane = tid & 31, nw = gs >> 5, w0 = (tid >> 5) & ~(nw - 1);
-        if (lane == 0) {
-            s_part[(parity * OT_BW + (tid >> 5)) * 2] = v0;
-            s_part[(parity * OT_BW + (tid >> 5)) * 2 + 1] = v1;
+        float x[R];
+        if (R == 2) {
+            float2* part = reinterpret_cast<float2*>(s_part) + parity * OT_BW;
+            if (lane == 0) part[tid >> 5] = make_float2(v[0], v[1 % R]);
+            group_barrier(gs, tid / gs);
+            // every aligned run of nw lanes holds the nw partials and combines them in the same tree
+            const float2 x2 = part[w0 + (lane & (nw - 1))];
+            x[0] = x2.x;
+            x[1 % R] = x2.y;
+        } else {
+            float4* part = reinterpret_cast<float4*>(s_part) + parity * OT_BW;
+            if (lane == 0) part[tid >> 5] = make_float4(v[0], v[1 % R], v[2 % R], 0.f);
+            group_barrier(gs, tid / gs);
+            const float4 x4 = part[w0 + (lane & (nw - 1))];
+            x[0] = x4.x;
+            x[1 % R] = x4.y;
+            x[2 % R] = x4.z;
         }
-        group_barrier(gs, tid / gs);
-        // every aligned run of nw lanes holds the nw partials and combines them in the same tree
-        const float2 x = reinterpret_cast<const float2*>(s_part)[parity * OT_BW + w0 + (lane & (nw - 1))];
-        float x0 = x.x, x1 = x.y;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             if (o < nw) {
-                const float a = __shfl_xor_sync(0xffffffffu, x0, o), b = __shfl_xor_sync(0xffffffffu, x1, o);
-                x0 = MAX ? fmaxf(x0, a) : x0 + a;
-                x1 = MAX ? fmaxf(x1, b) : x1 + b;
+                float a[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) a[r] = __shfl_xor_sync(0xffffffffu, x[r], o);
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[r] = MAX ? fmaxf(x[r], a[r]) : x[r] + a[r];
             }
         }
-        v0 = x0;
-        v1 = x1;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[r];
         parity ^= 1;   // the next reduction writes the other buffer (one barrier separates reuse)
     }
 }
@@ -328,8 +367,8 @@ __device__ __forceinline__ float hsum(f32x2 v) {
 // Every warp arrives once on a chunk's empty barrier when it no longer reads the
 // stage; thread OT_ISSUER issues the copies.
 struct Pipe {
-    float* stage;                 // [STAGES][2 * OT_BATCH_MAXM]
-    float4* rsc;                  // [STAGES][2 * OT_BW] scalars of the chunk's rows
+    float* stage;                 // [STAGES][OT_STAGE_FLOATS]
+    float4* rsc;                  // [STAGES][OT_RSC_STAGE] scalars of the chunk's rows
     unsigned long long* full;     // [STAGES]
     unsigned long long* empty;    // [STAGES] (OT_BW arrivals)
     volatile int* abort;          // set by the first expired wait; later waits give up at once
@@ -351,33 +390,33 @@ __device__ __forceinline__ void stage_release(const Pipe& P) {
     if ((threadIdx.x & 31) == 0) mbar_arrive_cnt(&P.empty[P.consumed % STAGES], 1u);
 }
 
-// Chunk k of a segment (thread OT_ISSUER): rows r_lo + 2 k NG .. (2 NG consecutive rows,
-// two per group) and their scalars, two bulk copies (rows are contiguous with
+// Chunk k of a segment (thread OT_ISSUER): rows r_lo + R k NG .. (R NG consecutive rows,
+// R per group) and their scalars, two bulk copies (rows are contiguous with
 // stride ld; all sizes and addresses 16-byte multiples).  The stage is taken
 // once every warp has released the chunk that used it before.  (No proxy fence
 // before a refill: the stage was only read through the generic proxy, and the
 // release/acquire pair on the empty barrier orders those reads first.)
-template <int STAGES>
+template <int STAGES, int R>
 __device__ __forceinline__ void issue_chunk(Pipe& P, const SegCtx& X, int k, const BatchArgs& A) {
     const long long n = P.issued;
     const int st = (int)(n % STAGES);
     if (n >= STAGES && !mbar_wait_ab(&P.empty[st], (unsigned)(((n - STAGES) / STAGES) & 1), A.timeout_ns, P.abort))
         abort_block(A, P);
     if (*P.abort) return;
-    const int r0 = X.r_lo + 2 * k * X.ng;
-    const int nr = min(2 * X.ng, X.r_hi - r0);
+    const int r0 = X.r_lo + R * k * X.ng;
+    const int nr = min(R * X.ng, X.r_hi - r0);
     const unsigned bytes = (unsigned)nr * (unsigned)X.ld * 4u, sbytes = (unsigned)nr * 16u;
     unsigned long long* bar = &P.full[st];
     mbar_arrive_expect_tx(bar, bytes + sbytes);
-    bulk_g2s(P.stage + (size_t)st * 2 * OT_BATCH_MAXM, X.Gp + (long long)r0 * X.ld, bytes, bar);
-    bulk_g2s(P.rsc + st * 2 * OT_BW, X.rs_cur + r0, sbytes, bar);
+    bulk_g2s(P.stage + (size_t)st * OT_STAGE_FLOATS, X.Gp + (long long)r0 * X.ld, bytes, bar);
+    bulk_g2s(P.rsc + st * OT_RSC_STAGE, X.rs_cur + r0, sbytes, bar);
     P.issued = n + 1;
 }
 
-// A row whose new potential is still to be written: lane i of a group's first
-// warp holds the rows with chunk-local index i mod 32 (two per chunk), and that
-// warp writes 32 of them at once (no serial chain of special functions on one
-// lane per chunk).
+// A row whose new potential is still to be written: lane R kk + r of a group's
+// first warp holds row r of the group's kk-th chunk in a window of 32 / R chunks,
+// and that warp writes the window's rows at once (no serial chain of special
+// functions on one lane per chunk).
 struct Pending {
     float S, F, al;
     int row;   // -1: none
@@ -399,136 +438,161 @@ __device__ __forceinline__ void finish_pending(const BatchArgs& A, const SegCtx&
     pd.row = -1;
 }
 
-// Row update of the two rows of a chunk held by a group (Eq.
+// Row update of the R rows of a chunk held by a group (Eq.
 // optimal_f_sinkhorn_logdomain in log2 units): S_r = sum_j 2^(gamma_j - kap c_rj + F_r)
 // around the previous potential F_r, new potential F_r - log2(S_r / alpha_r)
 // kept exactly as hi + lo (recorded in pd, written by finish_pending), column
-// contributions (alpha_r / S_r) e_rj added to acc.  An explicit max shift is used on the first sweep and whenever a row
-// sum leaves the safe range (then from the rows in global memory: the stage may
-// already be refilled).
-template <int STAGES>
+// contributions (alpha_r / S_r) e_rj added to acc.  An explicit max shift is used
+// on the first sweep and whenever a row sum leaves the safe range (then from the
+// rows in global memory: the stage may already be refilled).  V float4 slots per
+// thread and row cover the row (V = OT_BV for two rows, 3 for three).
+template <int STAGES, int R, int V>
 __device__ __forceinline__ void process_rows(const float* srow, const float4* srsc, const BatchArgs& A,
-                                             const SegCtx& X, int row, int k, const ColData& CR, float* s_part,
-                                             int& parity, f32x2 (&acc)[2 * OT_BV], f32x2 (&cmp)[2 * OT_BV],
+                                             const SegCtx& X, int row, int k, int kk, const ColData& CR,
+                                             float* s_part, int& parity, f32x2 (&acc)[2 * V], f32x2 (&cmp)[2 * V],
                                              float& l1, Pending& pd, Pipe& P) {
     const int GS = X.gs, gt = threadIdx.x & (GS - 1);
-    const bool two = row + 1 < X.r_hi;   // uniform over the group
-    // lanes of the group's first warp that hold the two rows until they are finished
-    const int ep0 = (2 * k) & 31, ep1 = ep0 + 1;
-    // a lone last row is processed twice (as both rows of the pair) and its second copy
-    // gets no weight: the hot loops carry no test for it
-    const float4 sc0 = srsc[0], sc1 = two ? srsc[1] : sc0;
-    const float al0 = sc0.z, al1 = sc1.z;
+    // rows of the chunk that exist (uniform over the group, >= 1); a missing row is
+    // processed as a copy of the first and gets no weight: the hot loops carry no test for it
+    const int nv = min(R, X.r_hi - row);
+    const int ep = R * kk;   // lanes of the group's first warp that hold the rows until they are finished
+    float4 sc[R];
+    const float4* c[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int rr = r < nv ? r : 0;
+        sc[r] = srsc[rr];
+        c[r] = reinterpret_cast<const float4*>(srow + rr * X.ld);
+    }
     const f32x2 nk2 = pk(-X.kap, -X.kap);
-    const float4* c0 = reinterpret_cast<const float4*>(srow);
-    const float4* c1 = reinterpret_cast<const float4*>(two ? srow + X.ld : srow);
-    float4 e0[OT_BV], e1[OT_BV];
-    float F0 = sc0.x, F1 = sc1.x, S0 = 0.f, S1 = 0.f;
+    float4 e[R][V];
+    float F[R], S[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) F[r] = sc[r].x;
     const bool first = X.t == 1;
     bool shifted = first;
     if (!shifted) {
-        const f32x2 F02 = pk(F0, F0), F12 = pk(F1, F1);
-        f32x2 S02 = pk(0.f, 0.f), S12 = pk(0.f, 0.f);
+        f32x2 F2[R], S2[R];
 #pragma unroll
-        for (int v = 0; v < OT_BV; ++v) {
+        for (int r = 0; r < R; ++r) {
+            F2[r] = pk(F[r], F[r]);
+            S2[r] = pk(0.f, 0.f);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
             const int g = gt + v * GS;
-            e0[v] = e1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) e[r][v] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g < X.ng4) {
                 const float4 gg = CR.gc[g], cc = CR.cf[g];
-                e0[v] = exps4(c0[g], gg, nk2, F02);
-                S02 = dot4x2(e0[v], cc, S02);
-                e1[v] = exps4(c1[g], gg, nk2, F12);
-                S12 = dot4x2(e1[v], cc, S12);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    e[r][v] = exps4(c[r][g], gg, nk2, F2[r]);
+                    S2[r] = dot4x2(e[r][v], cc, S2[r]);
+                }
             }
         }
         stage_release<STAGES>(P);
-        S0 = hsum(S02);
-        S1 = hsum(S12);
-        group_allreduce2<false>(S0, S1, GS, s_part, parity);
-        if (threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
-        if (gt == ep0) l1 += fabsf(fmaf(S0, sc0.y - 1.0f, S0 - al0));
-        if (two && gt == ep1) l1 += fabsf(fmaf(S1, sc1.y - 1.0f, S1 - al1));
-        // uniform over the group
-        shifted = !(S0 > 1e-30f && S0 < 1e30f) || (two && !(S1 > 1e-30f && S1 < 1e30f));
+#pragma unroll
+        for (int r = 0; r < R; ++r) S[r] = hsum(S2[r]);
+        group_allreduce<false, R>(S, GS, s_part, parity);
+        if (threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES, R>(P, X, k + STAGES, A);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r < nv && gt == ep + r) l1 += fabsf(fmaf(S[r], sc[r].y - 1.0f, S[r] - sc[r].z));
+            // uniform over the group
+            if (r < nv && !(S[r] > 1e-30f && S[r] < 1e30f)) shifted = true;
+        }
     }
     if (shifted) {
-        // explicit shifts F_r = -max_j (gamma_j - kap c_rj), both rows
-        const float4* r0 = first ? c0 : reinterpret_cast<const float4*>(X.Gp + (long long)row * X.ld);
-        const float4* r1 = first ? c1 : reinterpret_cast<const float4*>(X.Gp + (long long)(two ? row + 1 : row) * X.ld);
-        float m0 = -INFINITY, m1 = -INFINITY;
+        // explicit shifts F_r = -max_j (gamma_j - kap c_rj)
+        const float4* rp[R];
+        float mx[R];
 #pragma unroll
-        for (int v = 0; v < OT_BV; ++v) {
+        for (int r = 0; r < R; ++r) {
+            rp[r] = first ? c[r]
+                          : reinterpret_cast<const float4*>(X.Gp + (long long)(row + (r < nv ? r : 0)) * X.ld);
+            mx[r] = -INFINITY;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
             const int g = gt + v * GS;
-            e0[v] = e1[v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+            for (int r = 0; r < R; ++r) e[r][v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
             if (g < X.ng4) {
                 const float4 gg = CR.gc[g];
-                float4 c = r0[g];
-                float2 x01 = upk(fma2(pk(c.x, c.y), nk2, pk(gg.x, gg.y)));
-                float2 x23 = upk(fma2(pk(c.z, c.w), nk2, pk(gg.z, gg.w)));
-                e0[v] = make_float4(x01.x, x01.y, x23.x, x23.y);
-                m0 = fmaxf(m0, fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y)));
-                if (two) {
-                    c = r1[g];
-                    x01 = upk(fma2(pk(c.x, c.y), nk2, pk(gg.x, gg.y)));
-                    x23 = upk(fma2(pk(c.z, c.w), nk2, pk(gg.z, gg.w)));
-                    e1[v] = make_float4(x01.x, x01.y, x23.x, x23.y);
-                    m1 = fmaxf(m1, fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y)));
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float4 cv = rp[r][g];
+                    const float2 x01 = upk(fma2(pk(cv.x, cv.y), nk2, pk(gg.x, gg.y)));
+                    const float2 x23 = upk(fma2(pk(cv.z, cv.w), nk2, pk(gg.z, gg.w)));
+                    e[r][v] = make_float4(x01.x, x01.y, x23.x, x23.y);
+                    mx[r] = fmaxf(mx[r], fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y)));
                 }
             }
         }
         if (first) stage_release<STAGES>(P);
-        group_allreduce2<true>(m0, m1, GS, s_part, parity);
-        if (first && threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES>(P, X, k + STAGES, A);
-        F0 = m0 > -INFINITY ? -m0 : 0.f;
-        F1 = m1 > -INFINITY ? -m1 : 0.f;
-        f32x2 S02 = pk(0.f, 0.f), S12 = pk(0.f, 0.f);
+        group_allreduce<true, R>(mx, GS, s_part, parity);
+        if (first && threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES, R>(P, X, k + STAGES, A);
+        f32x2 S2[R];
 #pragma unroll
-        for (int v = 0; v < OT_BV; ++v) {
+        for (int r = 0; r < R; ++r) {
+            F[r] = mx[r] > -INFINITY ? -mx[r] : 0.f;
+            S2[r] = pk(0.f, 0.f);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
             const int g = gt + v * GS;
-            float4 x = e0[v];
-            x = make_float4(ex2(x.x + F0), ex2(x.y + F0), ex2(x.z + F0), ex2(x.w + F0));
-            e0[v] = x;
-            x = e1[v];
-            x = make_float4(ex2(x.x + F1), ex2(x.y + F1), ex2(x.z + F1), ex2(x.w + F1));
-            e1[v] = x;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float4 x = e[r][v];
+                e[r][v] = make_float4(ex2(x.x + F[r]), ex2(x.y + F[r]), ex2(x.z + F[r]), ex2(x.w + F[r]));
+            }
             if (g < X.ng4) {
                 const float4 cc = CR.cf[g];
-                S02 = dot4x2(e0[v], cc, S02);
-                S12 = dot4x2(e1[v], cc, S12);
+#pragma unroll
+                for (int r = 0; r < R; ++r) S2[r] = dot4x2(e[r][v], cc, S2[r]);
             }
         }
-        S0 = hsum(S02);
-        S1 = hsum(S12);
-        group_allreduce2<false>(S0, S1, GS, s_part, parity);
-    }
-    if (gt == ep0) {
-        pd.S = S0;
-        pd.F = F0;
-        pd.al = al0;
-        pd.row = row;
-    }
-    if (two && gt == ep1) {
-        pd.S = S1;
-        pd.F = F1;
-        pd.al = al1;
-        pd.row = row + 1;
-    }
-    const float u0 = (S0 > 1e-30f && S0 < 1e30f) ? __fdividef(al0, S0) : 0.f;
-    const float u1 = (two && S1 > 1e-30f && S1 < 1e30f) ? __fdividef(al1, S1) : 0.f;
-    const f32x2 u02 = pk(u0, u0), u12 = pk(u1, u1);
 #pragma unroll
-    for (int v = 0; v < OT_BV; ++v) {
-        kahan2(acc[2 * v], cmp[2 * v], u02, pk(e0[v].x, e0[v].y), u12, pk(e1[v].x, e1[v].y));
-        kahan2(acc[2 * v + 1], cmp[2 * v + 1], u02, pk(e0[v].z, e0[v].w), u12, pk(e1[v].z, e1[v].w));
+        for (int r = 0; r < R; ++r) S[r] = hsum(S2[r]);
+        group_allreduce<false, R>(S, GS, s_part, parity);
+    }
+    f32x2 u2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r < nv && gt == ep + r) {
+            pd.S = S[r];
+            pd.F = F[r];
+            pd.al = sc[r].z;
+            pd.row = row + r;
+        }
+        const float u = (r < nv && S[r] > 1e-30f && S[r] < 1e30f) ? __fdividef(sc[r].z, S[r]) : 0.f;
+        u2[r] = pk(u, u);
+    }
+    // (a slot past the row end holds zeros, so its sums stay zero: no test in the loop)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        f32x2 e01[R], e23[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            e01[r] = pk(e[r][v].x, e[r][v].y);
+            e23[r] = pk(e[r][v].z, e[r][v].w);
+        }
+        kahan_rows<R>(acc[2 * v], cmp[2 * v], u2, e01);
+        kahan_rows<R>(acc[2 * v + 1], cmp[2 * v + 1], u2, e23);
     }
 }
 
-// Rows [r_lo, r_hi) of one problem by all groups of the block.  Chunk k holds
-// rows r_lo + 2 (k NG + q) and the next one for group q; STAGES chunks are in
-// flight.  Returns false (uniformly) if a wait expired.
-template <int STAGES>
-__device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p, int r_lo, int r_hi, int t,
+// Rows [r_lo, r_hi) of one problem by all groups of the block, R rows per group
+// and chunk.  Chunk k holds rows r_lo + R (k NG + q) .. + R - 1 for group q;
+// STAGES chunks are in flight.  Returns false (uniformly) if a wait expired.
+template <int STAGES, int R>
+__device__ __forceinline__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p, int r_lo, int r_hi,
+                                          int t,
                              int GS, float* s_part, float* s_gc, float* s_cf, Pipe& P) {
+    constexpr int V = R == 2 ? OT_BV : 3;   // a row of a three-row chunk fills at most 3 slots
+    constexpr int W = 32 / R;               // chunks per window of pending rows
     const int NG = OT_BT / GS;
     const int tid = threadIdx.x, gt = tid & (GS - 1), q = tid / GS;
     const int cur = (t - 1) & 1, nxt = t & 1;
@@ -546,9 +610,9 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     X.r_hi = r_hi;
     X.t = t;
     X.kap = (float)(1.0 / ((double)d.eps * OT_LN2));
-    X.nchunks = (r_hi - r_lo + 2 * NG - 1) / (2 * NG);
+    X.nchunks = (r_hi - r_lo + R * NG - 1) / (R * NG);
     if (tid == OT_ISSUER) {
-        for (int k = 0; k < X.nchunks && k < STAGES; ++k) issue_chunk<STAGES>(P, X, k, A);
+        for (int k = 0; k < X.nchunks && k < STAGES; ++k) issue_chunk<STAGES, R>(P, X, k, A);
     }
     // stage the column data (every thread has finished with the previous segment's)
     __syncthreads();
@@ -562,15 +626,16 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     CR.gc = reinterpret_cast<const float4*>(s_gc);
     CR.cf = reinterpret_cast<const float4*>(s_cf);
     int parity = 0;
-    f32x2 acc[2 * OT_BV], cmp[2 * OT_BV];   // column contributions: compensated sums acc - (-cmp)
+    f32x2 acc[2 * V], cmp[2 * V];   // column contributions: compensated sums acc - (-cmp)
 #pragma unroll
-    for (int v = 0; v < 2 * OT_BV; ++v) acc[v] = cmp[v] = pk(0.f, 0.f);
+    for (int v = 0; v < 2 * V; ++v) acc[v] = cmp[v] = pk(0.f, 0.f);
     float l1 = 0.f;
     Pending pd;
     pd.S = pd.F = pd.al = 0.f;
     pd.row = -1;
     for (int k = 0; k < X.nchunks; ++k) {
-        const int row = r_lo + 2 * (k * NG + q);
+        const int kk = k % W;   // chunk index within the window of pending rows
+        const int row = r_lo + R * (k * NG + q);
         const int st = (int)(P.consumed % STAGES);
         const unsigned ph = (unsigned)((P.consumed / STAGES) & 1);
         if (!mbar_wait_ab(&P.full[st], ph, A.timeout_ns, P.abort)) abort_block(A, P);
@@ -578,20 +643,20 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
         // every warp keeps to the same sequence of group barriers and releases; the block
         // leaves together at the end of the segment)
         if (row < r_hi)   // uniform over the group
-            process_rows<STAGES>(P.stage + (size_t)st * 2 * OT_BATCH_MAXM + (size_t)(2 * q) * X.ld,
-                                 P.rsc + st * 2 * OT_BW + 2 * q, A, X, row, k, CR, s_part, parity, acc, cmp, l1, pd,
-                                 P);
+            process_rows<STAGES, R, V>(P.stage + (size_t)st * OT_STAGE_FLOATS + (size_t)(R * q) * X.ld,
+                                       P.rsc + st * OT_RSC_STAGE + R * q, A, X, row, k, kk, CR, s_part, parity,
+                                       acc, cmp, l1, pd, P);
         else
             stage_release<STAGES>(P);
-        // the group's first warp writes its 32 pending rows every 16 chunks and at the end
-        if (gt < 32 && ((k & 15) == 15 || k == X.nchunks - 1)) finish_pending(A, X, pd);
+        // the group's first warp writes the window's pending rows at its end and at the segment's end
+        if (gt < 32 && (kk == W - 1 || k == X.nchunks - 1)) finish_pending(A, X, pd);
         P.consumed += 1;
     }
     if (__syncthreads_or(*P.abort)) return false;
     // column contributions of this group (times the lo factors) and its L1 terms
-    if (r_lo + 2 * q < r_hi) {
+    if (r_lo + R * q < r_hi) {
 #pragma unroll
-        for (int v = 0; v < OT_BV; ++v) {
+        for (int v = 0; v < V; ++v) {
             const int g = gt + v * GS;
             if (g < X.ng4) {
                 const float4 cc = CR.cf[g];
@@ -610,17 +675,21 @@ __device__ bool rows_segment(const BatchArgs& A, const ot_problem_desc& d, int p
     return true;
 }
 
-template <int STAGES>
+// One launch solves the problems whose chunks hold R rows per group (chunk_rows);
+// the solver launches once per R, so that each launch carries one row engine.
+template <int STAGES, int R>
 __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_constant__ BatchArgs A) {
+    // a launch without problems of its kind leaves at once (every block alike)
+    if (A.nrows && A.nrows[2 * A.gs_shift + R - 2] == 0) return;
     extern __shared__ __align__(128) unsigned char dsm[];
-    float* s_stage = reinterpret_cast<float*>(dsm + BatchSmem::stage);                 // [STAGES][2 MAXM]
+    float* s_stage = reinterpret_cast<float*>(dsm + BatchSmem::stage);                 // [STAGES][OT_STAGE_FLOATS]
     float* s_gc = reinterpret_cast<float*>(dsm + BatchSmem::gc);                       // [MAXM]
     float* s_cf = reinterpret_cast<float*>(dsm + BatchSmem::cf);                       // [MAXM]
     long long* s_pref = reinterpret_cast<long long*>(dsm + BatchSmem::pref);           // [count+1]
-    int* s_m = reinterpret_cast<int*>(dsm + BatchSmem::msz);                           // [count]
-    int* s_act = reinterpret_cast<int*>(dsm + BatchSmem::act);                         // [count]
-    int* s_rw = reinterpret_cast<int*>(dsm + BatchSmem::rw);                           // [count]
-    __shared__ __align__(8) float s_part[2 * OT_BW * 2];
+    unsigned short* s_m = reinterpret_cast<unsigned short*>(dsm + BatchSmem::msz);     // [count]
+    unsigned short* s_rw = reinterpret_cast<unsigned short*>(dsm + BatchSmem::rw);     // [count]
+    unsigned char* s_act = reinterpret_cast<unsigned char*>(dsm + BatchSmem::act);     // [count]
+    __shared__ __align__(16) float s_part[2 * OT_BW * 4];
     __shared__ long long s_wsum[32];
     __shared__ double s_dred[OT_BW];
     __shared__ __align__(8) unsigned long long s_full[STAGES], s_empty[STAGES];
@@ -648,13 +717,16 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         fence_mbar_init();
     }
     for (int p = tid; p < count; p += OT_BT) {
-        s_m[p] = A.desc[p].m;
-        s_rw[p] = row_weight(A.desc[p].ld, A.gs_shift);
+        const int ld = A.desc[p].ld;
+        s_m[p] = (unsigned short)A.desc[p].m;
+        // row weight, 0 for the problems of the other launch
+        s_rw[p] = chunk_rows(row_slots(ld, A.gs_shift)) == R ? (unsigned short)row_weight(ld, A.gs_shift) : 0;
     }
     __syncthreads();
 
     // ---- per-problem marginal sums and validation (problems split over blocks)
     for (int p = B; p < count; p += Gd) {
+        if (!s_rw[p]) continue;   // uniform over the block
         const ot_problem_desc d = A.desc[p];
         const int m = d.m;
         const long long v0 = d.v_off;
@@ -725,7 +797,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         // ---------------- row phase
         // (the row scalars written last sweep by generic stores are read by bulk copies)
         if (tid == OT_ISSUER) asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (int p = tid; p < count; p += OT_BT) s_act[p] = A.active[p];
+        for (int p = tid; p < count; p += OT_BT) s_act[p] = (A.active[p] && s_rw[p]) ? 1 : 0;
         __syncthreads();
         batch_prefix(count, s_m, s_rw, s_act, true, s_pref, s_wsum);
         {
@@ -742,7 +814,7 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
                 if (r_lo >= r_hi) continue;
                 const ot_problem_desc d = A.desc[p];
                 const int gs = group_size(d.ld, A.gs_shift);   // tuned: a larger group takes fewer slots per thread
-                if (!rows_segment<STAGES>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, P)) goto fail;
+                if (!rows_segment<STAGES, R>(A, d, p, r_lo, r_hi, t, gs, s_part, s_gc, s_cf, P)) goto fail;
             }
         }
         asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -816,12 +888,13 @@ __global__ void __launch_bounds__(OT_BT, 1) batch_solve_kernel(const __grid_cons
         }
         if (!grid_sync(A.ctrl, Gd, A.timeout_ns, epoch)) goto fail;
         int any = 0;
-        for (int p = tid; p < count; p += OT_BT) any |= ((volatile int*)A.active)[p];
+        for (int p = tid; p < count; p += OT_BT) any |= s_rw[p] ? ((volatile int*)A.active)[p] : 0;
         if (!__syncthreads_or(any)) break;
     }
 
-    // ---------------- outputs: each block writes a share of all problems
+    // ---------------- outputs: each block writes a share of this launch's problems
     for (int p = B; p < count; p += Gd) {
+        if (!s_rw[p]) continue;
         const ot_problem_desc d = A.desc[p];
         const int m = d.m;
         const long long v0 = d.v_off;
@@ -845,6 +918,7 @@ fail:
         for (long long u = P.issued > STAGES ? P.issued - STAGES : 0; u < P.issued; ++u)
             if (!mbar_wait(&s_full[u % STAGES], (unsigned)((u / STAGES) & 1), A.timeout_ns)) break;
         for (int p = B; p < count; p += Gd) {
+            if (!s_rw[p]) continue;
             A.res[p].iters = -1;
             A.res[p].status = ld_volatile_int(&A.ctrl->status);
         }
@@ -936,8 +1010,10 @@ struct BatchHeader {
     int count;
     int max_m;
     long long total_m;
-    long long pad[6];
+    int nrows[2][2];   // problems with [group-size shift][rows per chunk - 2]
+    long long pad[4];
 };
+static_assert(sizeof(BatchHeader) == 64, "header layout");
 
 }  // namespace cyc
 
@@ -961,12 +1037,16 @@ extern "C" int ot_batch_prepare(const ot_problem_desc* descs, int count, void* w
         TM = TM > d.v_off + d.m ? TM : d.v_off + d.m;
         max_m = max_m > d.m ? max_m : d.m;
     }
+    int nrows[2][2] = {{0, 0}, {0, 0}};
+    for (int p = 0; p < count; ++p)
+        for (int sh = 0; sh < 2; ++sh) nrows[sh][chunk_rows(row_slots(descs[p].ld, sh)) - 2] += 1;
     if (ws_bytes < ot_batch_workspace_bytes(count, TM) || ((uintptr_t)workspace) % 256) return OT_ERR_WORKSPACE;
     BatchHeader h;
     memset(&h, 0, sizeof(h));
     h.count = count;
     h.max_m = max_m;
     h.total_m = TM;
+    memcpy(h.nrows, nrows, sizeof(nrows));
     cudaStream_t st = (cudaStream_t)stream;
     char* w = (char*)workspace;
     const BatchLayout L = batch_layout(count, TM);
@@ -1022,12 +1102,13 @@ static int encode_cfg(const BatchCfg& c) {
     return 1 + c.gs_shift + (ce << 1);
 }
 
-template <int STAGES>
+template <int STAGES, int R>
 static int launch_batch(const BatchArgs& A, cudaStream_t st) {
     const int sms = device_sms();
     if (sms <= 0) return OT_ERR_CUDA;
+    if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return OT_ERR_CUDA;
     const size_t smem = BatchSmem::total;
-    auto kern = batch_solve_kernel<STAGES>;
+    auto kern = batch_solve_kernel<STAGES, R>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return OT_ERR_CUDA;
     int nb = 0;
@@ -1049,8 +1130,9 @@ static int launch_batch(const BatchArgs& A, cudaStream_t st) {
 
 static int batch_solve_cfg(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
                            const ot_options* opt, double* w_all, double* z_all, ot_result* results, void* workspace,
-                           size_t ws_bytes, cudaStream_t st, const BatchCfg& C) {
+                           size_t ws_bytes, cudaStream_t st, const BatchCfg& C, int rows = 0) {
     char* base = (char*)workspace + a256(sizeof(BatchHeader));
+    const BatchHeader* hdr = (const BatchHeader*)workspace;
     const BatchLayout L = batch_layout(count, total_m);
     BatchArgs A;
     memset(&A, 0, sizeof(A));
@@ -1065,6 +1147,7 @@ static int batch_solve_cfg(int count, long long total_m, const float* G_all, con
     A.warm = opt->warm_start;
     A.gs_shift = C.gs_shift;
     A.check_every = C.check_every;
+    A.nrows = rows ? nullptr : &hdr->nrows[0][0];   // a single problem (rows given) has no prepared header
     A.w_out = w_all;
     A.z_out = z_all;
     A.res = results;
@@ -1081,8 +1164,12 @@ static int batch_solve_cfg(int count, long long total_m, const float* G_all, con
     A.gc = (float*)(base + L.gc);
     A.cf = (float*)(base + L.cf);
     A.R = (float*)(base + L.R);
-    if (cudaMemsetAsync(A.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return OT_ERR_CUDA;
-    return launch_batch<OT_STAGES_MAX>(A, st);
+    // the problems with two rows per chunk, then those with three (rows: only one of them)
+    if (rows != 3) {
+        const int rc = launch_batch<OT_STAGES_MAX, 2>(A, st);
+        if (rc != OT_OK || rows == 2) return rc;
+    }
+    return launch_batch<OT_STAGES_MAX, 3>(A, st);
 }
 
 static int batch_check_args(int count, long long total_m, const float* G_all, const float* a_all, const float* b_all,
@@ -1133,7 +1220,8 @@ int batch_single_solve(int m, int N, const float* G, int ld, const float* a, con
     if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     BatchCfg C;
     decode_cfg(0, opt->check_every, C);
-    return batch_solve_cfg(1, m, G, a, b, opt, w, z, out, workspace, ws_bytes, st, C);
+    return batch_solve_cfg(1, m, G, a, b, opt, w, z, out, workspace, ws_bytes, st, C,
+                           chunk_rows(row_slots(ld, C.gs_shift)));
 }
 
 }  // namespace cyc

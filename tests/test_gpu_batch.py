@@ -26,9 +26,10 @@ from oracle import sinkhorn as OS
 
 pytestmark = pytest.mark.gpu
 
-# (m, N, seed, eps_frac): several m not divisible by 4
+# (m, N, seed, eps_frac): several m not divisible by 4; 257 (one-warp groups), 701 (two warps)
+# and 1103 (four warps) fill three float4 slots per thread and take three rows per chunk
 CASES = [(37, 3, 1, 0.05), (60, 4, 0, 0.05), (130, 5, 2, 0.03), (257, 2, 3, 0.02), (11, 6, 4, 0.05),
-         (401, 8, 5, 0.01), (1, 4, 6, 0.05), (203, 3, 7, 0.01)]
+         (401, 8, 5, 0.01), (1, 4, 6, 0.05), (203, 3, 7, 0.01), (701, 3, 8, 0.03), (1103, 2, 9, 0.03)]
 
 
 @pytest.fixture(scope="module")
