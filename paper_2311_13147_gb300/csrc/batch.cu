@@ -1,18 +1,20 @@
-// Batches of independent cyclic problems (uneven m and N): fold and cyclic
-// Sinkhorn for all of them in one persistent launch each.
+// Batches of independent cyclic problems (uneven m and N): fold in one launch,
+// cyclic Sinkhorn in two persistent launches (one per rows-per-chunk class,
+// see chunk_rows).
 //
 // Solver (Algorithm 2 per problem, log domain, the same iteration and stopping
 // rule as ot_sinkhorn_reduced).  Two bounded grid barriers per sweep:
 //
-//  row phase    The rows of the still-active problems form one index space
-//               weighted by row length; every block takes a contiguous,
-//               equally weighted range of it (recomputed identically in every
-//               block each sweep, so finished problems free their share).  A
-//               block streams chunks of rows (two per thread group) through
-//               shared-memory stages filled by bulk copies, together with the
-//               rows' scalars (previous potential, its lo factor, the row
-//               marginal).  A group of GS threads owns a fixed set of
-//               columns; it forms the exponentials of its two rows around the
+//  row phase    The rows of the launch's still-active problems form one index
+//               space weighted by estimated row cost; every block takes a
+//               contiguous, equally weighted range of it (recomputed
+//               identically in every block each sweep, so finished problems
+//               free their share).  A block streams chunks of rows (two or
+//               three per thread group) through shared-memory stages filled by
+//               bulk copies, together with the rows' scalars (previous
+//               potential, its lo factor, the row marginal).  A group of GS
+//               threads owns a fixed set of columns; it forms the
+//               exponentials of its chunk rows around the
 //               previous potentials in registers, releases the stage (so that
 //               the next copy starts while the row sums are reduced), then
 //               writes the new row potentials and adds the column
