@@ -498,15 +498,18 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
                                              float* s_part, int& parity, f32x2 (&acc)[2 * V], f32x2 (&cmp)[2 * V],
                                              float& l1, Pending& pd, Pipe& P) {
     const int GS = X.gs, gt = threadIdx.x & (GS - 1);
-    // rows of the chunk that exist (uniform over the group, >= 1); a missing row is
-    // processed as a copy of the first and gets no weight: the hot loops carry no test for it
-    const int nv = min(R, X.r_hi - row);
+    // row r of the chunk exists iff ok[r] (uniform over the group; the caller guarantees row 0);
+    // a missing row is processed as a copy of the first and gets no weight: the hot loops carry
+    // no test for it
+    bool ok[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) ok[r] = r == 0 || row + r < X.r_hi;
     const int ep = R * kk;   // lanes of the group's first warp that hold the rows until they are finished
     float4 sc[R];
     const float4* c[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rr = r < nv ? r : 0;
+        const int rr = ok[r] ? r : 0;
         sc[r] = srsc[rr];
         c[r] = reinterpret_cast<const float4*>(srow + rr * X.ld);
     }
@@ -545,9 +548,9 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
         if (threadIdx.x == OT_ISSUER && k + STAGES < X.nchunks) issue_chunk<STAGES, R>(P, X, k + STAGES, A);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (r < nv && gt == ep + r) l1 += fabsf(fmaf(S[r], sc[r].y - 1.0f, S[r] - sc[r].z));
+            if (ok[r] && gt == ep + r) l1 += fabsf(fmaf(S[r], sc[r].y - 1.0f, S[r] - sc[r].z));
             // uniform over the group
-            if (r < nv && !(S[r] > 1e-30f && S[r] < 1e30f)) shifted = true;
+            if (ok[r] && !(S[r] > 1e-30f && S[r] < 1e30f)) shifted = true;
         }
     }
     if (shifted) {
@@ -557,7 +560,7 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             rp[r] = first ? c[r]
-                          : reinterpret_cast<const float4*>(X.Gp + (long long)(row + (r < nv ? r : 0)) * X.ld);
+                          : reinterpret_cast<const float4*>(X.Gp + (long long)(row + (ok[r] ? r : 0)) * X.ld);
             mx[r] = -INFINITY;
         }
 #pragma unroll
@@ -607,13 +610,13 @@ __device__ __forceinline__ void process_rows(const float* srow, const float4* sr
     f32x2 u2[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (r < nv && gt == ep + r) {
+        if (ok[r] && gt == ep + r) {
             pd.S = S[r];
             pd.F = F[r];
             pd.al = sc[r].z;
             pd.row = row + r;
         }
-        const float u = (r < nv && S[r] > 1e-30f && S[r] < 1e30f) ? __fdividef(sc[r].z, S[r]) : 0.f;
+        const float u = (ok[r] && S[r] > 1e-30f && S[r] < 1e30f) ? __fdividef(sc[r].z, S[r]) : 0.f;
         u2[r] = pk(u, u);
     }
     // (a slot past the row end holds zeros, so its sums stay zero: no test in the loop)
