@@ -28,8 +28,9 @@ flushed (a 512 MB write) before every timed step.
 
 ``--workload batch``: 512 independent ring-cloud problems, n ~ U[1024, 16384],
 N ~ U{2, 3, 4, 6, 8}, Dirichlet(0.5) marginals, eps = 0.01 * max C, folded
-from the point coordinates and solved to 1e-6 in one persistent launch each
-(fold + solve replayed as a CUDA graph, launch configuration autotuned first).
+from the point coordinates (one launch) and solved to 1e-6 in two persistent
+launches, one per rows-per-chunk class (fold + solve replayed as a CUDA graph,
+launch configuration autotuned first).
 The 17.7 GB of folded costs exceed L2, so no flush is needed.
 
 ``--workload precision``: 8 costs of that batch (m from 158 to 8162), each

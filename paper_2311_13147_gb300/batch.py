@@ -3,8 +3,9 @@
 Packs a list of problems (block size m, order N, eps, base points and
 marginals) into the flat device buffers the C ABI expects -- descriptors,
 one float2 point buffer, one cost buffer with 4-aligned rows, one vector
-buffer per marginal / potential -- and runs ot_batch_fold + ot_batch_solve
-(one persistent launch each).  ``BatchSolver.autotune()`` picks the solver's
+buffer per marginal / potential -- and runs ot_batch_fold (one launch) and
+ot_batch_solve (two persistent launches: problems with two and with three
+rows per thread group and chunk).  ``BatchSolver.autotune()`` picks the solver's
 launch configuration for the batch; ``BatchSolver.capture()`` records the fold
 and the solve in a CUDA graph that ``replay()`` launches again.
 """
