@@ -195,7 +195,7 @@ __device__ __forceinline__ bool mbar_wait_ab(unsigned long long* bar, unsigned p
 
 // Thread-group size of a problem's rows: the smallest power of two >= 32 whose
 // OT_BV float4 slots per thread cover the row stride (one size larger per shift).
-__host__ __device__ __forceinline__ int group_size(int ld, int shift) {
+__host__ __device__ __forceinline__ constexpr int group_size(int ld, int shift) {
     int gs = 32;
     while (gs < OT_BT && gs * 4 * OT_BV < ld) gs <<= 1;
     gs <<= shift;
@@ -203,13 +203,25 @@ __host__ __device__ __forceinline__ int group_size(int ld, int shift) {
 }
 
 // Float4 slots of a row that each thread of its group covers (1 .. OT_BV).
-__host__ __device__ __forceinline__ int row_slots(int ld, int shift) {
+__host__ __device__ __forceinline__ constexpr int row_slots(int ld, int shift) {
     const int gs = group_size(ld, shift);
     return (ld + 4 * gs - 1) / (4 * gs);
 }
 
 // Rows per group and chunk (see OT_STAGE_FLOATS).
-__host__ __device__ __forceinline__ int chunk_rows(int slots) { return slots == 3 ? 3 : 2; }
+__host__ __device__ __forceinline__ constexpr int chunk_rows(int slots) { return slots == 3 ? 3 : 2; }
+
+// Every chunk fits its stage: R rows of ld floats for each of the OT_BT / GS groups, and
+// their R * OT_BT / GS row scalars, for every row stride and group-size policy.
+constexpr bool stages_hold_every_chunk() {
+    for (int sh = 0; sh < 2; ++sh)
+        for (int ld = 4; ld <= OT_BATCH_MAXM; ld += 4) {
+            const int gs = group_size(ld, sh), rows = chunk_rows(row_slots(ld, sh)) * (OT_BT / gs);
+            if ((long long)rows * ld > OT_STAGE_FLOATS || rows > OT_RSC_STAGE) return false;
+        }
+    return true;
+}
+static_assert(stages_hold_every_chunk(), "a chunk exceeds its shared-memory stage");
 
 // Estimated cost of one row of a problem, the unit of the row phase's work split:
 // a chunk costs its group a fixed part (OT_ROW_FIXED slots) plus half a slot per
