@@ -15,7 +15,6 @@ Tolerances:
   plan);
 * iterations within 3% (+2) of the oracle's on its own FP64 fold.
 """
-import math
 
 import numpy as np
 import pytest

@@ -15,7 +15,6 @@ import pytest
 import torch
 
 from paper_2311_13147_gb300 import inputs as I
-from oracle import rot as OR
 from oracle import sinkhorn as OS
 
 pytestmark = pytest.mark.gpu

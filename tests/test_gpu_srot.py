@@ -14,7 +14,6 @@ import pytest
 import torch
 
 from paper_2311_13147_gb300 import inputs as I
-from oracle import rot as OR
 from oracle import srot as SR
 
 pytestmark = pytest.mark.gpu

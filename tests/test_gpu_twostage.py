@@ -9,7 +9,6 @@
   FP64 (row L1 <= tol + 2e-7, column L1 <= 1e-6) and the objective within
   1e-5 of the oracle's plain full Sinkhorn.
 """
-import math
 
 import numpy as np
 import pytest

@@ -6,7 +6,6 @@ that the order is a permutation whose second half mirrors the first, a
 distance matrix recomputed with scipy from the ordered pixel positions, and
 the oracle's full Sinkhorn against its reduced solve.
 """
-import math
 
 import numpy as np
 import pytest
