@@ -74,3 +74,34 @@ def test_struct_layouts_match_header():
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         fields = re.findall(r"\b([A-Za-z_0-9]+)\s*(?:\[\d+\])?\s*[;,]", body)
         assert [f[0] for f in cls._fields_] == fields
+
+
+def test_batch_prepare_validates_the_table_on_the_host(libpath):
+    """ot_batch_prepare checks every descriptor and the workspace before any device call, so the
+    refusals below need no GPU (the workspace address is never dereferenced)."""
+    from paper_2311_13147_gb300 import cyclicot as cy
+    L = cy._batch_lib()
+    D = cy.ot_problem_desc
+    fake = ctypes.c_void_p(1 << 20)          # 256-byte aligned, never touched
+
+    def prep(descs, ws=fake, nbytes=None):
+        arr = (D * len(descs))(*descs)
+        total_m = max(d.v_off + d.m for d in descs)
+        n = cy.ot_batch_workspace_bytes(len(descs), total_m) if nbytes is None else nbytes
+        return L.ot_batch_prepare(arr, len(descs), ws, n, None)
+
+    good = [D(100, 4, 0.1, 100, 0, 0, 0, 100), D(37, 3, 0.05, 40, 10000, 100, 200, 237)]
+    assert prep(good, ws=None) == cy.OT_ERR_ARG
+    assert prep([D(100, 4, 0.1, 102, 0, 0, 0, 100)]) == cy.OT_ERR_ARG        # row stride not a multiple of 4
+    assert prep([D(100, 4, 0.1, 96, 0, 0, 0, 100)]) == cy.OT_ERR_ARG         # stride shorter than the row
+    assert prep([D(8193, 2, 0.1, 8196, 0, 0, 0, 8193)]) == cy.OT_ERR_ARG     # block wider than 8192
+    assert prep([D(100, 4, 0.0, 100, 0, 0, 0, 100)]) == cy.OT_ERR_ARG        # eps <= 0
+    assert prep([D(100, 257, 0.1, 100, 0, 0, 0, 100)]) == cy.OT_ERR_ARG      # N above 256
+    assert prep([D(100, 4, 0.1, 100, 2, 0, 0, 100)]) == cy.OT_ERR_ARG        # cost offset not 16-byte aligned
+    assert prep([D(0, 4, 0.1, 4, 0, 0, 0, 0)]) == cy.OT_ERR_ARG              # empty block
+    need = cy.ot_batch_workspace_bytes(2, 137)
+    assert prep(good, nbytes=need - 1) == cy.OT_ERR_WORKSPACE
+    assert prep(good, ws=ctypes.c_void_p((1 << 20) + 16)) == cy.OT_ERR_WORKSPACE   # not 256-byte aligned
+    arr = (D * 1)(good[0])
+    assert L.ot_batch_prepare(arr, 0, fake, need, None) == cy.OT_ERR_ARG
+    assert L.ot_batch_prepare(arr, 1025, fake, need, None) == cy.OT_ERR_ARG
