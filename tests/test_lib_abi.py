@@ -105,3 +105,44 @@ def test_batch_prepare_validates_the_table_on_the_host(libpath):
     arr = (D * 1)(good[0])
     assert L.ot_batch_prepare(arr, 0, fake, need, None) == cy.OT_ERR_ARG
     assert L.ot_batch_prepare(arr, 1025, fake, need, None) == cy.OT_ERR_ARG
+
+
+def test_solver_and_fold_arguments_are_checked_on_the_host(libpath):
+    """The fold and the reduced and full solvers refuse bad arguments before any device call, so
+    each refusal below returns at once without touching the (fake) pointers."""
+    from paper_2311_13147_gb300 import cyclicot as cy
+    L = cy.lib()
+    P = ctypes.c_void_p(1 << 20)            # 256-byte aligned, never dereferenced
+    odd = ctypes.c_void_p((1 << 20) + 4)   # not 16-byte aligned
+    NULL = None
+
+    def opts(**kw):
+        o = cy.options(0.1)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def red(m=8, N=2, a=P, b=P, G=P, opt="ok", w=P, z=P, out=P):
+        o = ctypes.byref(opts()) if opt == "ok" else opt
+        return L.ot_sinkhorn_reduced(m, N, a, b, G, o, w, z, out, P, 1 << 20, NULL)
+
+    for bad in (dict(m=0), dict(N=0), dict(a=NULL), dict(b=NULL), dict(G=NULL), dict(w=NULL), dict(z=NULL),
+                dict(out=NULL), dict(opt=NULL), dict(G=odd)):
+        assert red(**bad) == cy.OT_ERR_ARG, bad
+    for field, value in (("eps", 0.0), ("max_iter", 0), ("check_every", 0), ("tol_l1", -1e-9), ("stop_norm", 7),
+                         ("precision", 3), ("tile_override", 1)):
+        assert red(opt=ctypes.byref(opts(**{field: value}))) == cy.OT_ERR_ARG, field
+
+    def full(n=16, a=P, b=P, C=P, X=NULL, Y=NULL, f=P, g=P, out=P):
+        return L.ot_sinkhorn_full(n, a, b, C, X, Y, ctypes.byref(opts()), f, g, out, P, 1 << 20, NULL)
+
+    for bad in (dict(n=0), dict(a=NULL), dict(b=NULL), dict(f=NULL), dict(g=NULL), dict(out=NULL),
+                dict(C=NULL), dict(C=NULL, X=P), dict(C=odd)):
+        assert full(**bad) == cy.OT_ERR_ARG, bad
+
+    def fold(mode=cy.OT_SOFTMIN, m=8, N=2, C=P, x=NULL, y=NULL, eps=0.1, G=P):
+        return L.ot_fold_cost(mode, m, N, C, x, y, eps, G, NULL, NULL)
+
+    for bad in (dict(m=0), dict(N=0), dict(G=NULL), dict(mode=9), dict(eps=0.0), dict(C=NULL), dict(C=NULL, x=P)):
+        assert fold(**bad) == cy.OT_ERR_ARG, bad
+    assert fold(mode=cy.OT_MIN, N=256) == cy.OT_ERR_UNSUPPORTED   # k* is one byte
