@@ -146,3 +146,51 @@ def test_solver_and_fold_arguments_are_checked_on_the_host(libpath):
     for bad in (dict(m=0), dict(N=0), dict(G=NULL), dict(mode=9), dict(eps=0.0), dict(C=NULL), dict(C=NULL, x=P)):
         assert fold(**bad) == cy.OT_ERR_ARG, bad
     assert fold(mode=cy.OT_MIN, N=256) == cy.OT_ERR_UNSUPPORTED   # k* is one byte
+
+
+def test_lot_srot_and_unfold_arguments_are_checked_on_the_host(libpath):
+    """The reduced LOT and C-SROT solvers and the unfold refuse bad arguments (and, for the two
+    solvers, short or misaligned workspaces and sizes above their limits) before any device call."""
+    from paper_2311_13147_gb300 import cyclicot as cy
+    P = ctypes.c_void_p(1 << 20)            # 256-byte aligned, never dereferenced
+    NULL = None
+    ok = ctypes.byref(cy.options(0.1))
+
+    Lt = cy._lot_lib()
+    need = Lt.ot_lot_workspace_bytes(2, 16)
+
+    def lot(count=2, m=16, N=3, a=P, b=P, G=P, opt=ok, S=P, u=P, v=P, out=P, ws=P, nbytes=need):
+        return Lt.ot_lot_reduced(count, m, N, a, b, G, opt, S, u, v, out, ws, nbytes, NULL)
+
+    for bad in (dict(count=0), dict(m=0), dict(N=0), dict(a=NULL), dict(b=NULL), dict(G=NULL), dict(opt=NULL),
+                dict(S=NULL), dict(u=NULL), dict(v=NULL), dict(out=NULL),
+                dict(opt=ctypes.byref(cy.options(0.1, max_iter=0)))):
+        assert lot(**bad) == cy.OT_ERR_ARG, bad
+    assert lot(m=5121) == cy.OT_ERR_UNSUPPORTED
+    for bad in (dict(ws=NULL), dict(nbytes=need - 1), dict(ws=ctypes.c_void_p((1 << 20) + 64))):
+        assert lot(**bad) == cy.OT_ERR_WORKSPACE, bad
+
+    Ls = cy._srot_lib()
+    need = Ls.ot_srot_workspace_bytes(16, 2)
+
+    def srot(m=16, N=2, a=P, b=P, C=P, opt=ok, w=P, z=P, out=P, ws=P, nbytes=need):
+        return Ls.ot_srot_reduced(m, N, a, b, C, opt, w, z, out, ws, nbytes, NULL)
+
+    for bad in (dict(m=0), dict(N=0), dict(a=NULL), dict(b=NULL), dict(C=NULL), dict(opt=NULL), dict(w=NULL),
+                dict(z=NULL), dict(out=NULL), dict(opt=ctypes.byref(cy.options(0.0))),
+                dict(opt=ctypes.byref(cy.options(0.1, max_iter=0))),
+                dict(opt=ctypes.byref(cy.options(0.1, tol=-1.0)))):
+        assert srot(**bad) == cy.OT_ERR_ARG, bad
+    assert srot(m=1024, N=9) == cy.OT_ERR_UNSUPPORTED   # N m above 8192
+    for bad in (dict(ws=NULL), dict(nbytes=need - 1), dict(ws=ctypes.c_void_p((1 << 20) + 64))):
+        assert srot(**bad) == cy.OT_ERR_WORKSPACE, bad
+
+    L = cy.lib()
+
+    def unfold(mode=cy.OT_PLAN_EROT, m=8, N=2, S=P, z=P, C=P, x=NULL, y=NULL, k=P, eps=0.1, T=P):
+        return L.ot_unfold_plan(mode, m, N, S, z, C, x, y, k, eps, 0, T, NULL)
+
+    for bad in (dict(m=0), dict(N=0), dict(S=NULL), dict(T=NULL), dict(mode=7), dict(z=NULL), dict(eps=0.0),
+                dict(C=NULL), dict(C=NULL, x=P), dict(mode=cy.OT_PLAN_LOT, k=NULL),
+                dict(mode=cy.OT_PLAN_LOT, N=256)):
+        assert unfold(**bad) == cy.OT_ERR_ARG, bad
