@@ -194,3 +194,37 @@ def test_lot_srot_and_unfold_arguments_are_checked_on_the_host(libpath):
                 dict(C=NULL), dict(C=NULL, x=P), dict(mode=cy.OT_PLAN_LOT, k=NULL),
                 dict(mode=cy.OT_PLAN_LOT, N=256)):
         assert unfold(**bad) == cy.OT_ERR_ARG, bad
+
+
+def test_value_and_kernel_domain_arguments_are_checked_on_the_host(libpath):
+    """ot_value_and_grad and the kernel-domain solver refuse bad arguments and workspaces before any
+    device call (the unrolled adjoint only for its own missing inputs)."""
+    from paper_2311_13147_gb300 import cyclicot as cy
+    P = ctypes.c_void_p(1 << 20)            # 256-byte aligned, never dereferenced
+    NULL = None
+    L = cy.lib()
+    big = 1 << 24
+
+    def value(m=8, N=2, a=P, b=P, C=P, x=NULL, y=NULL, G=NULL, w=P, z=P, eps=0.1, adj=cy.OT_ADJ_ENVELOPE, T=0,
+              out=P, dC=NULL, dx=NULL, dy=NULL, ws=P, nbytes=big):
+        return L.ot_value_and_grad(m, N, a, b, C, x, y, G, w, z, eps, adj, T, out, NULL, NULL, dC, dx, dy, ws, nbytes,
+                                   NULL)
+
+    for bad in (dict(m=0), dict(N=0), dict(a=NULL), dict(b=NULL), dict(out=NULL), dict(eps=0.0), dict(C=NULL),
+                dict(C=NULL, x=P), dict(dx=P), dict(C=NULL, x=P, y=P, dC=P), dict(adj=5), dict(w=NULL), dict(z=NULL),
+                dict(adj=cy.OT_ADJ_UNROLLED, T=10), dict(adj=cy.OT_ADJ_UNROLLED, G=P, T=0)):
+        assert value(**bad) == cy.OT_ERR_ARG, bad
+    for bad in (dict(ws=NULL), dict(nbytes=64), dict(ws=ctypes.c_void_p((1 << 20) + 8))):
+        assert value(**bad) == cy.OT_ERR_WORKSPACE, bad
+
+    K = cy._kd_lib()
+    need = K.ot_kdomain_workspace_bytes(256)
+
+    def kd(m=256, G=P, ld=256, eps=0.1, nrhs=8, a=P, b=P, iters=4, z=P, ws=P, nbytes=need):
+        return K.ot_kdomain_solve(m, G, ld, eps, nrhs, a, b, iters, z, NULL, ws, nbytes, NULL)
+
+    for bad in (dict(m=0), dict(m=16385, ld=16385), dict(G=NULL), dict(ld=255), dict(eps=0.0), dict(nrhs=0),
+                dict(nrhs=65), dict(a=NULL), dict(b=NULL), dict(iters=0), dict(z=NULL), dict(ws=NULL)):
+        assert kd(**bad) == cy.OT_ERR_ARG, bad
+    for bad in (dict(nbytes=need - 1), dict(ws=ctypes.c_void_p((1 << 20) + 128))):
+        assert kd(**bad) == cy.OT_ERR_WORKSPACE, bad
