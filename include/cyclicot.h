@@ -161,6 +161,9 @@ size_t ot_workspace_bytes(int op, int m_or_n, int N, const ot_options* opt);
  *  and y [m][2] (targets), C_k[i][j] = |x_i - R^k y_j|^2, R = rotation by
  *  2*pi/N (computed in FP32).
  *  Outputs: G [m][m] float; kstar [m][m] uint8 (OT_MIN only, N <= 255).
+ *  Returns OT_ERR_ARG (m or N <= 0, G NULL, an unknown mode, eps <= 0 with
+ *  OT_SOFTMIN, no cost source), OT_ERR_UNSUPPORTED (OT_MIN with N > 255: k*
+ *  is one byte) or OT_ERR_CUDA, all before anything is enqueued.
  */
 int ot_fold_cost(int mode, int m, int N, const float* C_base, const float* x,
                  const float* y, float eps, float* G, uint8_t* kstar, void* stream);
@@ -238,6 +241,9 @@ int ot_sinkhorn_full(int n, const float* a, const float* b, const float* C,
  *  dense = 0: T is the first block row [N][m][m] (T_0..T_{N-1});
  *  dense = 1: T is the n x n matrix, T[r*m+i][c*m+j] = T_{(c-r) mod N}[i][j]
  *      (Lemma 1, Eq. blkstr_optimal_solution).  Index map is exact.
+ *  Returns OT_ERR_ARG (m or N <= 0, S_or_w or T NULL, an unknown mode;
+ *  OT_PLAN_LOT without kstar or with N > 255; OT_PLAN_EROT without z, with
+ *  eps <= 0 or without a cost source) or OT_ERR_CUDA.
  */
 int ot_unfold_plan(int mode, int m, int N, const void* S_or_w, const double* z,
                    const float* C_base, const float* x, const float* y,
