@@ -162,8 +162,8 @@ size_t ot_workspace_bytes(int op, int m_or_n, int N, const ot_options* opt);
  *  2*pi/N (computed in FP32).
  *  Outputs: G [m][m] float; kstar [m][m] uint8 (OT_MIN only, N <= 255).
  *  Returns OT_ERR_ARG (m or N <= 0, G NULL, an unknown mode, eps <= 0 with
- *  OT_SOFTMIN, no cost source), OT_ERR_UNSUPPORTED (OT_MIN with N > 255: k*
- *  is one byte) or OT_ERR_CUDA, all before anything is enqueued.
+ *  OT_SOFTMIN, no cost source) or OT_ERR_UNSUPPORTED (OT_MIN with N > 255: k*
+ *  is one byte) before anything is enqueued, OT_ERR_CUDA on a failed launch.
  */
 int ot_fold_cost(int mode, int m, int N, const float* C_base, const float* x,
                  const float* y, float eps, float* G, uint8_t* kstar, void* stream);
