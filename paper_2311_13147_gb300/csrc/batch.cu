@@ -164,10 +164,7 @@ __device__ __forceinline__ void kahan_rows(f32x2& sum, f32x2& nc, const f32x2 (&
     sum = t;
 }
 
-// Compensated (Kahan) addition on both lanes of the contribution u0 e0 + u1 e1:
-// sum - nc carries the running total of the added values to about one rounding,
-// however many rows a thread accumulates (nc is the negated compensation, so the
-// contribution and the compensation enter through two FMAs).
+// The two-row engine's compensated addition: kahan_rows<2> with scalar arguments.
 __device__ __forceinline__ void kahan2(f32x2& sum, f32x2& nc, f32x2 u0, f32x2 e0, f32x2 u1, f32x2 e1) {
     const f32x2 y = fma2(u1, e1, fma2(u0, e0, nc));
     const f32x2 t = add2(sum, y);
@@ -352,7 +349,8 @@ __device__ __forceinline__ void group_allreduce(float (&v)[R], int gs, float* s_
     }
 }
 
-// All-reduce of two values (the two rows of a chunk) over a group.
+// The two-row engine's all-reduce of two values (the two rows of a chunk) over a
+// group: group_allreduce<MAX, 2> with scalar arguments.
 template <bool MAX>
 __device__ __forceinline__ void group_allreduce2(float& v0, float& v1, int gs, float* s_part, int& parity) {
 #pragma unroll
